@@ -1,0 +1,194 @@
+/*
+ * cc.h -- C ABI of the GB300 median-consensus sweep library (libcc.so).
+ *
+ * Method: graph-aware median consensus clustering (Hussain, Halappanavar,
+ * Chatterjee, Radicchi, Fortunato, Azad, "Parallel Algorithms for Median
+ * Consensus Clustering in Complex Networks", arXiv 2408.11331).  Given a graph
+ * and k input partitions P_1..P_k of its n vertices, the library starts from
+ * singleton clusters and runs synchronous greedy local-move sweeps that lower
+ * F(C) = sum_i Mirkin(C, P_i) (Eq. objective1), each vertex considering only
+ * the clusters of its neighbours (Eq. objective4) and scored by the exact
+ * integer change of Eq. objective3.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Host pointers are borrowed for the duration of the call and copied; the
+ *   library never keeps them.  The _dev variants take device pointers under the
+ *   same rule.  All output buffers are caller-allocated.
+ * - The context owns every device buffer it allocates and frees them in
+ *   cc_destroy.  All device work of a context runs on one CUDA stream (its
+ *   own, or the one given to cc_set_stream); entry points that return host
+ *   values synchronise that stream.
+ * - Every call returns a cc_status; nothing is thrown across the ABI.  After a
+ *   failure, cc_last_error(ctx) describes it.  CC_ERR_CUDA leaves the context
+ *   unusable; the other errors leave it as it was before the call.
+ * - Objective values use ordered pairs (the Mirkin distance counts each
+ *   disagreeing pair twice, Methods); the unordered count is F / 2.
+ * - Cluster ids are founding-vertex ids: the singleton start gives C[v] = v and
+ *   ids are never renumbered, because ties between candidates go to the
+ *   smaller id.
+ * - Arithmetic is integer and exact.  Gains are int32, which requires
+ *   3 k n + k < 2^31 (else CC_ERR_OVERFLOW); objectives are int64.
+ * - Not thread-safe per context; distinct contexts may be used concurrently.
+ */
+#ifndef CC_H
+#define CC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_ctx cc_ctx;
+
+typedef enum {
+    CC_OK = 0,
+    CC_ERR_INVALID = 1,    /* malformed argument: null pointer, n < 1, k < 1, nnz < 0, CSR offsets
+                              not starting at 0 / not ending at nnz / decreasing, column out of range */
+    CC_ERR_OOM = 2,        /* a device allocation failed */
+    CC_ERR_CUDA = 3,       /* a CUDA runtime call or kernel failed */
+    CC_ERR_OVERFLOW = 4,   /* 3 k n + k >= 2^31: an int32 gain could overflow */
+    CC_ERR_TABLE_FULL = 5, /* the contingency hash ran out of slots (bounded probing gave up) */
+    CC_ERR_TIMEOUT = 6     /* reserved: a bounded device wait gave up */
+} cc_status;
+
+typedef struct {
+    int32_t max_sweeps;     /* sweep limit used when cc_run_until_converged gets max_sweeps <= 0;
+                               default 20 */
+    int32_t debug_checks;   /* 1: after every sweep recompute F from scratch on the device and
+                               fail with CC_ERR_INVALID if it differs from the incremental F */
+    int32_t table_log2;     /* log2 of the contingency hash capacity; 0 = automatic
+                               (capacity >= 3 k n, so no sweep can fill it) */
+    int32_t reserved[5];    /* must be zero */
+} cc_options;
+
+/* Per-sweep record.  Field meanings follow the synchronous sweep of the
+ * Parallel algorithm section with its validation checks fixed as:
+ *   proposals  |P|: vertices whose best graph-restricted move (Eq. objective4)
+ *              has dD < 0 against the sweep-start state (ties: smaller id)
+ *   p1         |P1|: proposals kept by the singleton guard (a move between two
+ *              singleton clusters a -> b is kept only if b < a)
+ *   dF_p1      exact F(C with all of P1 applied) - F(C); 0 when P1 is empty
+ *   fallback   1 if P1 was empty or dF_p1 >= 0 and the locally dominant
+ *              matching of P was committed instead (each cluster keeps the
+ *              least (dD, v) of the proposals leaving or entering it; a move is
+ *              committed iff it holds the least key at both its clusters)
+ *   moves      moves committed
+ *   F          objective after the sweep                                     */
+typedef struct {
+    int64_t proposals;
+    int64_t p1;
+    int64_t dF_p1;
+    int64_t fallback;
+    int64_t moves;
+    int64_t F;
+} cc_sweep_info;
+
+/* Fills *opt with the defaults (max_sweeps 20, no debug checks, automatic
+ * table size).  Never fails for a non-null opt. */
+void cc_default_options(cc_options* opt);
+
+/* Creates a context for one consensus job and puts it at the singleton start
+ * (The algorithm: Initialization).
+ *   n        number of vertices, >= 1
+ *   nnz      number of CSR entries, >= 0 (an undirected edge appears twice)
+ *   row_off  int64[n + 1] host, row_off[0] = 0, non-decreasing, row_off[n] = nnz
+ *   col      int32[nnz]   host, neighbour ids in [0, n); self-loops and repeated
+ *            entries are allowed and ignored (candidate sets are sets)
+ *   k        number of input partitions, >= 1
+ *   labels   int32[k * n] host, partition-major: labels[i * n + v] is v's
+ *            cluster in P_i; any int32 values, only equality matters
+ *   opt      options, or NULL for the defaults
+ *   out      receives the new context; set to NULL on failure
+ * The graph and labels are copied to the device and stay resident; labels
+ * are compacted per partition and stored vertex-major (the n x k membership
+ * matrix of the complexity analysis).  Errors: CC_ERR_INVALID,
+ * CC_ERR_OVERFLOW, CC_ERR_OOM, CC_ERR_CUDA (then *out is NULL and nothing
+ * leaks). */
+cc_status cc_create(int32_t n, int64_t nnz, const int64_t* row_off, const int32_t* col, int32_t k,
+                    const int32_t* labels, const cc_options* opt, cc_ctx** out);
+
+/* As cc_create, with row_off, col and labels in device memory (same layouts).
+ * stream: the cudaStream_t to use (NULL: the context creates its own).  The
+ * device buffers are read on that stream before the call returns. */
+cc_status cc_create_dev(int32_t n, int64_t nnz, const int64_t* row_off_dev, const int32_t* col_dev,
+                        int32_t k, const int32_t* labels_dev, const cc_options* opt, void* stream,
+                        cc_ctx** out);
+
+/* Uses the given cudaStream_t (NULL: the context's own) for later calls. */
+cc_status cc_set_stream(cc_ctx* ctx, void* stream);
+
+/* Returns the context to the singleton start (C[v] = v, F = F0) with the
+ * inputs kept resident; the sweep history is cleared. */
+cc_status cc_reset(cc_ctx* ctx);
+
+/* Replaces the consensus with C (host int32[n], cluster ids in [0, n); any
+ * ids, not only founding vertices) and rebuilds sizes, contingency counts and
+ * F from it; the sweep history is kept.  This is a warm start (for instance
+ * resuming from a saved consensus: the state of a run is C alone, everything
+ * else is derived from C and the inputs).  The paper always starts from
+ * singletons (The algorithm: Initialization); this call generalises that step.
+ * Errors: CC_ERR_INVALID (an id outside [0, n)), CC_ERR_CUDA. */
+cc_status cc_set_cluster_ids(cc_ctx* ctx, const int32_t* C);
+
+/* Runs one synchronous sweep (Parallel algorithm section) and, if info is not
+ * NULL, writes its record.  A sweep with no proposal changes nothing.
+ * Errors: CC_ERR_TABLE_FULL, CC_ERR_CUDA, CC_ERR_INVALID (debug check). */
+cc_status cc_sweep(cc_ctx* ctx, cc_sweep_info* info);
+
+/* Runs sweeps until one has no proposal (the stopping condition of The
+ * algorithm) or max_sweeps sweeps ran (max_sweeps <= 0: the option's limit).
+ * The whole loop is one CUDA-graph submission (max_sweeps sweeps unrolled, each
+ * skipped on the device once the run has stopped) and one synchronisation.
+ * *sweeps_done (may be NULL) counts every sweep run, the final empty one
+ * included.  Errors as cc_sweep. */
+cc_status cc_run_until_converged(cc_ctx* ctx, int32_t max_sweeps, int32_t* sweeps_done);
+
+/* Device time of each sweep of the last cc_run_until_converged / cc_sweep
+ * call, from CUDA events recorded inside its graph on the context's stream:
+ * sweep_ms[s] covers sweep s (all its kernels), propose_ms[s] its proposal
+ * kernel.  At most max entries are written to each non-NULL array; *count
+ * receives the number of sweeps that ran. */
+cc_status cc_last_run_timing(cc_ctx* ctx, int32_t max, float* sweep_ms, float* propose_ms, int32_t* count);
+
+/* Number of CUDA kernels the context has launched since creation (nodes of
+ * its sweep graphs included, whether or not a stopped sweep skipped them). */
+cc_status cc_launch_count(const cc_ctx* ctx, int64_t* out);
+
+/* Copies the records of the sweeps run since creation or the last reset,
+ * oldest first: at most max entries into out, the total count into *count. */
+cc_status cc_history(cc_ctx* ctx, int32_t max, cc_sweep_info* out, int32_t* count);
+
+/* F(C) = sum_i Mirkin(C, P_i), ordered pairs (Eq. objective1), as kept
+ * incrementally by the sweeps. */
+cc_status cc_objective(cc_ctx* ctx, int64_t* out);
+
+/* F(C) recomputed from scratch on the device from C and the labels
+ * (k sum_c |c|^2 + sum_ij |P_ij|^2 - 2 sum_{c,i,j} n(c,i,j)^2), for checks. */
+cc_status cc_objective_recompute(cc_ctx* ctx, int64_t* out);
+
+/* The consensus as int32[n] (caller-allocated host buffer), clusters
+ * renumbered 0..b-1 in order of first appearance by vertex index. */
+cc_status cc_consensus_labels(cc_ctx* ctx, int32_t* out);
+
+/* The raw cluster ids (founding vertices) as int32[n] host, for parity checks. */
+cc_status cc_cluster_ids(cc_ctx* ctx, int32_t* out);
+
+/* Device pointer to the context's int32[n] cluster-id array (valid until the
+ * next call that modifies the context or cc_destroy); for zero-copy readers. */
+cc_status cc_cluster_ids_dev(cc_ctx* ctx, const int32_t** out);
+
+/* Message of the last failure on this context ("" if none).  Owned by the
+ * context; valid until the next call on it.  A NULL ctx gives the message of
+ * the last failed creation in this thread. */
+const char* cc_last_error(const cc_ctx* ctx);
+
+/* Frees every resource of the context.  NULL is allowed. */
+void cc_destroy(cc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_H */

@@ -1,0 +1,226 @@
+"""ctypes binding of libcc.so -- argument marshalling only.
+
+Every function here mirrors one entry point of include/cc.h under the same
+name; the work itself runs in the library's CUDA kernels.  There is no CPU
+fallback: if libcc.so is missing or cannot be loaded, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcc.so")
+
+CC_OK = 0
+STATUS_NAMES = {0: "CC_OK", 1: "CC_ERR_INVALID", 2: "CC_ERR_OOM", 3: "CC_ERR_CUDA", 4: "CC_ERR_OVERFLOW",
+                5: "CC_ERR_TABLE_FULL", 6: "CC_ERR_TIMEOUT"}
+
+# Every symbol include/cc.h declares; the CPU test suite checks the library exports them.
+EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", "cc_reset", "cc_set_cluster_ids", "cc_sweep",
+           "cc_run_until_converged", "cc_last_run_timing", "cc_launch_count", "cc_history", "cc_objective", "cc_objective_recompute",
+           "cc_consensus_labels", "cc_cluster_ids", "cc_cluster_ids_dev", "cc_last_error", "cc_destroy")
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class cc_options(ctypes.Structure):
+    _fields_ = [("max_sweeps", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
+                ("table_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class cc_sweep_info(ctypes.Structure):
+    _fields_ = [("proposals", ctypes.c_int64), ("p1", ctypes.c_int64), ("dF_p1", ctypes.c_int64),
+                ("fallback", ctypes.c_int64), ("moves", ctypes.c_int64), ("F", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing; build it with `python paper_2408_11331_gb300/build.py` "
+                          "(nvcc, sm_103a). There is no CPU fallback.")
+    lib = ctypes.CDLL(path)
+    c = ctypes
+    P = c.c_void_p
+    lib.cc_default_options.restype = None
+    lib.cc_default_options.argtypes = [c.POINTER(cc_options)]
+    lib.cc_create.restype = c.c_int
+    lib.cc_create.argtypes = [c.c_int32, c.c_int64, P, P, c.c_int32, P, c.POINTER(cc_options), c.POINTER(P)]
+    lib.cc_create_dev.restype = c.c_int
+    lib.cc_create_dev.argtypes = [c.c_int32, c.c_int64, P, P, c.c_int32, P, c.POINTER(cc_options), P,
+                                  c.POINTER(P)]
+    lib.cc_set_stream.restype = c.c_int
+    lib.cc_set_stream.argtypes = [P, P]
+    lib.cc_reset.restype = c.c_int
+    lib.cc_reset.argtypes = [P]
+    lib.cc_set_cluster_ids.restype = c.c_int
+    lib.cc_set_cluster_ids.argtypes = [P, P]
+    lib.cc_sweep.restype = c.c_int
+    lib.cc_sweep.argtypes = [P, c.POINTER(cc_sweep_info)]
+    lib.cc_run_until_converged.restype = c.c_int
+    lib.cc_run_until_converged.argtypes = [P, c.c_int32, c.POINTER(c.c_int32)]
+    lib.cc_last_run_timing.restype = c.c_int
+    lib.cc_last_run_timing.argtypes = [P, c.c_int32, P, P, c.POINTER(c.c_int32)]
+    lib.cc_launch_count.restype = c.c_int
+    lib.cc_launch_count.argtypes = [P, c.POINTER(c.c_int64)]
+    lib.cc_history.restype = c.c_int
+    lib.cc_history.argtypes = [P, c.c_int32, c.POINTER(cc_sweep_info), c.POINTER(c.c_int32)]
+    lib.cc_objective.restype = c.c_int
+    lib.cc_objective.argtypes = [P, c.POINTER(c.c_int64)]
+    lib.cc_objective_recompute.restype = c.c_int
+    lib.cc_objective_recompute.argtypes = [P, c.POINTER(c.c_int64)]
+    lib.cc_consensus_labels.restype = c.c_int
+    lib.cc_consensus_labels.argtypes = [P, P]
+    lib.cc_cluster_ids.restype = c.c_int
+    lib.cc_cluster_ids.argtypes = [P, P]
+    lib.cc_cluster_ids_dev.restype = c.c_int
+    lib.cc_cluster_ids_dev.argtypes = [P, c.POINTER(P)]
+    lib.cc_last_error.restype = c.c_char_p
+    lib.cc_last_error.argtypes = [P]
+    lib.cc_destroy.restype = None
+    lib.cc_destroy.argtypes = [P]
+    return lib
+
+
+lib = load_library()
+
+
+def _check(status: int, ctx=None):
+    if status != CC_OK:
+        msg = lib.cc_last_error(ctx)
+        raise CCError(status, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p(0)
+
+
+def cc_default_options() -> cc_options:
+    o = cc_options()
+    lib.cc_default_options(ctypes.byref(o))
+    return o
+
+
+def cc_create(row_off, col, labels, options: cc_options | None = None):
+    """Host arrays: row_off int64[n+1], col int32[nnz], labels int32[k, n] -> ctx handle."""
+    row_off = np.ascontiguousarray(row_off, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    if labels.ndim != 2:
+        raise ValueError("labels must be int32[k, n]")
+    k, n = labels.shape
+    if len(row_off) != n + 1:
+        raise ValueError("row_off must have n + 1 entries")
+    ctx = ctypes.c_void_p()
+    st = lib.cc_create(n, len(col), _ptr(row_off), _ptr(col), k, _ptr(labels),
+                       ctypes.byref(options) if options is not None else None, ctypes.byref(ctx))
+    _check(st, None)
+    return ctx
+
+
+def cc_create_dev(n: int, nnz: int, row_off_ptr: int, col_ptr: int, k: int, labels_ptr: int,
+                  options: cc_options | None = None, stream: int = 0):
+    """Device pointers (integers, e.g. torch ``data_ptr()``) -> ctx handle."""
+    ctx = ctypes.c_void_p()
+    st = lib.cc_create_dev(n, nnz, ctypes.c_void_p(row_off_ptr), ctypes.c_void_p(col_ptr), k,
+                           ctypes.c_void_p(labels_ptr), ctypes.byref(options) if options is not None else None,
+                           ctypes.c_void_p(stream or None), ctypes.byref(ctx))
+    _check(st, None)
+    return ctx
+
+
+def cc_set_stream(ctx, stream: int = 0):
+    _check(lib.cc_set_stream(ctx, ctypes.c_void_p(stream or None)), ctx)
+
+
+def cc_reset(ctx):
+    _check(lib.cc_reset(ctx), ctx)
+
+
+def cc_set_cluster_ids(ctx, C):
+    C = np.ascontiguousarray(C, dtype=np.int32)
+    _check(lib.cc_set_cluster_ids(ctx, _ptr(C)), ctx)
+
+
+def cc_sweep(ctx) -> dict:
+    info = cc_sweep_info()
+    _check(lib.cc_sweep(ctx, ctypes.byref(info)), ctx)
+    return info.as_dict()
+
+
+def cc_run_until_converged(ctx, max_sweeps: int = 0) -> int:
+    done = ctypes.c_int32(0)
+    _check(lib.cc_run_until_converged(ctx, max_sweeps, ctypes.byref(done)), ctx)
+    return done.value
+
+
+def cc_last_run_timing(ctx):
+    """(sweep_ms float32[s], propose_ms float32[s]) of the last run."""
+    count = ctypes.c_int32(0)
+    _check(lib.cc_last_run_timing(ctx, 0, None, None, ctypes.byref(count)), ctx)
+    a = np.zeros(max(count.value, 1), np.float32)
+    b = np.zeros(max(count.value, 1), np.float32)
+    _check(lib.cc_last_run_timing(ctx, count.value, _ptr(a), _ptr(b), ctypes.byref(count)), ctx)
+    return a[: count.value], b[: count.value]
+
+
+def cc_launch_count(ctx) -> int:
+    out = ctypes.c_int64(0)
+    _check(lib.cc_launch_count(ctx, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def cc_history(ctx) -> list:
+    count = ctypes.c_int32(0)
+    _check(lib.cc_history(ctx, 0, None, ctypes.byref(count)), ctx)
+    buf = (cc_sweep_info * max(count.value, 1))()
+    _check(lib.cc_history(ctx, count.value, buf, ctypes.byref(count)), ctx)
+    return [buf[i].as_dict() for i in range(count.value)]
+
+
+def cc_objective(ctx) -> int:
+    out = ctypes.c_int64(0)
+    _check(lib.cc_objective(ctx, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def cc_objective_recompute(ctx) -> int:
+    out = ctypes.c_int64(0)
+    _check(lib.cc_objective_recompute(ctx, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def cc_consensus_labels(ctx, n: int, out: np.ndarray | None = None) -> np.ndarray:
+    out = np.empty(n, np.int32) if out is None else out
+    _check(lib.cc_consensus_labels(ctx, _ptr(out)), ctx)
+    return out
+
+
+def cc_cluster_ids(ctx, n: int, out: np.ndarray | None = None) -> np.ndarray:
+    out = np.empty(n, np.int32) if out is None else out
+    _check(lib.cc_cluster_ids(ctx, _ptr(out)), ctx)
+    return out
+
+
+def cc_cluster_ids_dev(ctx) -> int:
+    p = ctypes.c_void_p()
+    _check(lib.cc_cluster_ids_dev(ctx, ctypes.byref(p)), ctx)
+    return p.value or 0
+
+
+def cc_last_error(ctx=None) -> str:
+    m = lib.cc_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def cc_destroy(ctx):
+    lib.cc_destroy(ctx)

@@ -1,0 +1,170 @@
+// Internal declarations shared by the CUDA translation units of libcc.so.
+//
+// Device data layout (one consensus job):
+//   off   int64[n+1]   CSR row offsets            col  int32[nnz]  neighbours
+//   G     int32[n][kp] compacted label ids, vertex-major, kp = k rounded up to 4 so
+//                      that each row is 16-byte aligned; g = i*n + rep where rep is
+//                      the least vertex carrying that label in partition i, so g
+//                      identifies (partition, label) and g < k*n. Padding = -1.
+//   C     int32[n]     cluster id of each vertex (founding-vertex ids)
+//   size  int32[n]     cluster sizes, indexed by cluster id
+//   table Slot[cap]    the contingency counts n(c, i, l) as an open-addressing
+//                      hash with linear probing, key = c << 32 | g, cap = 2^p.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cc.h"
+
+namespace ccg {
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr int kWarpsPerBlock = 8;
+constexpr int kBlock = kWarpsPerBlock * 32;
+constexpr int kTile = 256;  // vertices claimed at once by a block of the proposal kernel
+
+// One contingency entry: the (cluster, label id) key, its count and the
+// delta staged by the current sweep.  16 bytes, read as one vector load.
+struct __align__(16) Slot {
+    unsigned long long key;
+    int cnt;
+    int dlt;
+};
+
+// Device-resident control block of a context.
+struct DevState {
+    unsigned long long nprop;    // |P| of the current sweep
+    unsigned long long np1;      // |P1|
+    long long dF;                // staged objective change
+    long long dF_p1;             // dF of P1 as evaluated
+    long long F;                 // current objective
+    unsigned long long moves;    // moves committed in the current sweep
+    unsigned long long used;     // occupied table slots
+    long long live;              // keys with a non-zero count
+    unsigned long long tile_ctr; // next vertex tile of the proposal kernel
+    long long partition_sq;      // sum_i sum_j |P_ij|^2
+    long long recompute;         // output of the full objective reduction
+    int mode;                    // 0 nothing to commit, 1 commit P1, 2 matching
+    int skip;                    // 1: this sweep does nothing (the run has stopped)
+    int stop;                    // 1: the run has stopped
+    int rebuild;                 // 1: a table rebuild is pending
+    int err;                     // cc_status of a device-side failure (first one wins)
+    int sweeps;                  // sweeps recorded since creation / reset
+    int run_sweeps;              // sweeps in the current run
+    int run_limit;               // sweep limit of the current run
+};
+
+// Arguments of the sweep kernels (passed by value).
+struct SweepArgs {
+    int n, k, kp;
+    long long nnz;
+    const long long* off;
+    const int* col;
+    const int* G;
+    int* C;
+    int* size;
+    int* dsize;                 // staged size deltas
+    unsigned long long* best;   // matching keys per cluster
+    Slot* table;
+    unsigned long long mask;    // cap - 1
+    unsigned long long thresh;  // rebuild when used slots exceed this
+    int* pv;                    // proposal list: vertex,
+    int* pa;                    //   source cluster,
+    int* pb;                    //   target cluster,
+    int* pg;                    //   gain dD
+    unsigned char* pflag;       //   1 if kept by the singleton guard
+    unsigned int* pslot;        //   table slots of (a, g_i(v)) and (b, g_i(v)), 2 per (j, i)
+    DevState* st;
+    cc_sweep_info* hist;
+    int hist_cap;
+};
+
+// 64-bit finaliser of MurmurHash3 (Austin Appleby, public domain).
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z ^= z >> 33;
+    z *= 0xff51afd7ed558ccdull;
+    z ^= z >> 33;
+    z *= 0xc4ceb9fe1a85ec53ull;
+    z ^= z >> 33;
+    return z;
+}
+
+__device__ __forceinline__ unsigned long long ckey(int c, int g)
+{
+    return ((unsigned long long)(unsigned)c << 32) | (unsigned)g;
+}
+
+__device__ __forceinline__ void set_err(DevState* st, int code)
+{
+    atomicCAS(&st->err, 0, code);
+}
+
+// Count stored under key (0 if absent).  Read-only use during a kernel that
+// does not modify the table, so the non-coherent path is allowed.
+__device__ __forceinline__ int table_count_ro(const Slot* t, unsigned long long mask, unsigned long long key)
+{
+    unsigned long long h = mix64(key) & mask;
+    for (unsigned long long p = 0; p <= mask; ++p) {
+        ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(t + h));
+        if (e.x == key) return (int)(unsigned)(e.y & 0xffffffffull);
+        if (e.x == kEmpty) return 0;
+        h = (h + 1) & mask;
+    }
+    return 0;
+}
+
+// Slot holding key, or -1 (coherent loads; the key must not be inserted concurrently).
+__device__ __forceinline__ long long table_find(const Slot* t, unsigned long long mask, unsigned long long key)
+{
+    unsigned long long h = mix64(key) & mask;
+    for (unsigned long long p = 0; p <= mask; ++p) {
+        unsigned long long k = *reinterpret_cast<const volatile unsigned long long*>(&t[h].key);
+        if (k == key) return (long long)h;
+        if (k == kEmpty) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// Slot holding key, inserting it (count 0, delta 0) if absent.  *inserted is
+// set when this call created the slot.  Returns -1 if the table is full.
+__device__ __forceinline__ long long table_find_or_insert(Slot* t, unsigned long long mask,
+                                                          unsigned long long key, bool* inserted)
+{
+    *inserted = false;
+    unsigned long long h = mix64(key) & mask;
+    for (unsigned long long p = 0; p <= mask; ++p) {
+        unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&t[h].key);
+        if (k == key) return (long long)h;
+        if (k == kEmpty) {
+            unsigned long long old = atomicCAS(&t[h].key, kEmpty, key);
+            if (old == kEmpty) { *inserted = true; return (long long)h; }
+            if (old == key) return (long long)h;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// ---- launch wrappers (setup.cu) ----
+cudaError_t launch_validate(int n, long long nnz, const long long* off, const int* col, DevState* st,
+                            cudaStream_t s);
+cudaError_t launch_compact_labels(int n, int k, int kp, const int* labels, int* G, void* lmap,
+                                  unsigned long long lmask, DevState* st, cudaStream_t s);
+cudaError_t launch_init_state(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_state_from_ids(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_table_rebuild(const SweepArgs& a, bool conditional, cudaStream_t s);
+cudaError_t launch_objective_recompute(const SweepArgs& a, cudaStream_t s);
+
+// ---- launch wrappers (sweep.cu) ----
+cudaError_t launch_run_begin(DevState* st, int limit, cudaStream_t s);
+// One sweep (13 kernels); prop0/prop1 (may be null) are recorded around the proposal kernel.
+constexpr int kKernelsPerSweep = 13;
+constexpr int kKernelsPerRebuild = 4;
+cudaError_t launch_sweep(const SweepArgs& a, int grid, cudaStream_t s, cudaEvent_t prop0, cudaEvent_t prop1);
+size_t propose_smem_bytes(int kp);
+cudaError_t prepare_propose(int kp, int* blocks_per_sm);
+
+}  // namespace ccg

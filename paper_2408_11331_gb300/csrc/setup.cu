@@ -1,0 +1,304 @@
+// Setup of one consensus job (The algorithm: Initialization) and the table
+// maintenance kernels: input validation, per-partition label compaction into
+// the vertex-major membership matrix, the singleton state, the contingency
+// hash build, and the from-scratch objective used for checks.
+#include <climits>
+
+#include "cc_internal.cuh"
+
+namespace ccg {
+
+namespace {
+
+constexpr int kSetupBlock = 256;
+
+inline int grid_for(long long work, int per_block = kSetupBlock, int max_blocks = 152 * 16)
+{
+    long long b = (work + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+// (partition, raw label) -> least vertex carrying it, and the class size.
+struct __align__(16) LSlot {
+    unsigned long long key;
+    int rep;
+    int cnt;
+};
+
+__device__ __forceinline__ long long warp_sum64(long long x)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Block-wide sum of x, added to *out by one thread.  Every thread of the block calls it.
+__device__ void block_add64(long long x, long long* out)
+{
+    __shared__ long long part[32];
+    x = warp_sum64(x);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long y = lane < (int)(blockDim.x >> 5) ? part[lane] : 0;
+        y = warp_sum64(y);
+        if (lane == 0 && y != 0) atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)y);
+    }
+    __syncthreads();
+}
+
+__global__ void k_validate(int n, long long nnz, const long long* __restrict__ off,
+                           const int* __restrict__ col, DevState* st)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long v = t0; v <= n; v += stride) {
+        long long o = off[v];
+        bool bad = (v == 0 && o != 0) || (v == n && o != nnz) || (v < n && off[v + 1] < o);
+        if (bad) set_err(st, CC_ERR_INVALID);
+    }
+    for (long long e = t0; e < nnz; e += stride) {
+        int u = col[e];
+        if (u < 0 || u >= n) set_err(st, CC_ERR_INVALID);
+    }
+}
+
+__global__ void k_lmap_clear(LSlot* m, unsigned long long cap)
+{
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += stride) {
+        m[s].key = kEmpty;
+        m[s].rep = INT_MAX;
+        m[s].cnt = 0;
+    }
+}
+
+__device__ __forceinline__ long long lmap_slot(LSlot* m, unsigned long long mask, unsigned long long key, bool insert)
+{
+    unsigned long long h = mix64(key) & mask;
+    for (unsigned long long p = 0; p <= mask; ++p) {
+        unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&m[h].key);
+        if (k == key) return (long long)h;
+        if (k == kEmpty) {
+            if (!insert) return -1;
+            unsigned long long old = atomicCAS(&m[h].key, kEmpty, key);
+            if (old == kEmpty || old == key) return (long long)h;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// labels is partition-major: entry t = i*n + v.
+__global__ void k_label_insert(int n, int k, const int* __restrict__ labels, LSlot* m, unsigned long long mask,
+                               DevState* st)
+{
+    const long long total = (long long)n * k;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const int i = (int)(t / n), v = (int)(t - (long long)i * n);
+        const unsigned long long key = ((unsigned long long)(unsigned)i << 32) | (unsigned)labels[t];
+        long long s = lmap_slot(m, mask, key, true);
+        if (s < 0) { set_err(st, CC_ERR_TABLE_FULL); continue; }
+        atomicMin(&m[s].rep, v);
+        atomicAdd(&m[s].cnt, 1);
+    }
+}
+
+// G[v][i] = i*n + rep(i, label).  Tiles of 32 vertices x up to 32 partitions are
+// transposed through shared memory so both the label reads and the row writes
+// are coalesced.
+__global__ void k_label_assign(int n, int k, int kp, const int* __restrict__ labels, const LSlot* m,
+                               unsigned long long mask, int* __restrict__ G, DevState* st)
+{
+    __shared__ int tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    const long long vt = ((long long)n + 31) / 32, it = ((long long)kp + 31) / 32;
+    for (long long b = blockIdx.x; b < vt * it; b += gridDim.x) {
+        const long long v0 = (b / it) * 32;
+        const int i0 = (int)(b % it) * 32;
+        for (int r = ty; r < 32; r += 8) {
+            const int i = i0 + r;
+            const long long v = v0 + tx;
+            int g = -1;
+            if (i < k && v < n) {
+                const unsigned long long key = ((unsigned long long)(unsigned)i << 32) | (unsigned)labels[(long long)i * n + v];
+                long long s = lmap_slot(const_cast<LSlot*>(m), mask, key, false);
+                if (s < 0) set_err(st, CC_ERR_INVALID);
+                else g = (int)((long long)i * n + m[s].rep);
+            }
+            tile[r][tx] = g;
+        }
+        __syncthreads();
+        for (int r = ty; r < 32; r += 8) {
+            const long long v = v0 + r;
+            const int i = i0 + tx;
+            if (v < n && i < kp) G[v * kp + i] = tile[tx][r];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_label_sumsq(const LSlot* m, unsigned long long cap, DevState* st)
+{
+    long long acc = 0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += stride) {
+        long long c = m[s].cnt;
+        acc += c * c;
+    }
+    block_add64(acc, &st->partition_sq);
+}
+
+__global__ void k_init_state(int n, int* C, int* size, int* dsize, unsigned long long* best)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        C[v] = (int)v;
+        size[v] = 1;
+        dsize[v] = 0;
+        best[v] = kEmpty;
+    }
+}
+
+// Sizes from a given consensus; ids outside [0, n) set an error.
+__global__ void k_sizes_from_ids(int n, const int* __restrict__ C, int* size, int* dsize,
+                                 unsigned long long* best, DevState* st)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        size[v] = 0;
+        dsize[v] = 0;
+        best[v] = kEmpty;
+    }
+}
+
+__global__ void k_count_sizes(int n, const int* __restrict__ C, int* size, DevState* st)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int c = C[v];
+        if (c < 0 || c >= n) set_err(st, CC_ERR_INVALID);
+        else atomicAdd(&size[c], 1);
+    }
+}
+
+__global__ void k_table_clear(Slot* t, unsigned long long cap, const DevState* st, int conditional)
+{
+    if (conditional && (!st->rebuild || st->err)) return;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += stride)
+        reinterpret_cast<ulonglong2*>(t)[s] = make_ulonglong2(kEmpty, 0ull);
+}
+
+// Inserts (C[v], g_i(v)) with count +1 for every (v, i); counts new slots.
+__global__ void k_table_build(SweepArgs a, int conditional)
+{
+    DevState* st = a.st;
+    if (conditional && (!st->rebuild || st->err)) return;
+    const long long total = (long long)a.n * a.k;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
+        const long long t = base + threadIdx.x;
+        bool ins = false;
+        if (t < total) {
+            const int v = (int)(t / a.k), i = (int)(t - (long long)v * a.k);
+            const unsigned long long key = ckey(a.C[v], a.G[(long long)v * a.kp + i]);
+            long long s = table_find_or_insert(a.table, a.mask, key, &ins);
+            if (s < 0) set_err(st, CC_ERR_TABLE_FULL);
+            else atomicAdd(&a.table[s].cnt, 1);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ins);
+        if (lane == 0 && m) atomicAdd(&st->used, (unsigned long long)__popc(m));
+    }
+}
+
+__global__ void k_table_reset_counters(DevState* st, int conditional)
+{
+    if (conditional && (!st->rebuild || st->err)) return;
+    st->used = 0;
+}
+
+__global__ void k_table_done(DevState* st, int conditional)
+{
+    if (conditional && (!st->rebuild || st->err)) return;
+    st->live = (long long)st->used;
+    st->rebuild = 0;
+}
+
+__global__ void k_objective_recompute(SweepArgs a)
+{
+    long long acc = 0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (unsigned long long v = t0; v < (unsigned long long)a.n; v += stride) {
+        long long s = a.size[v];
+        acc += (long long)a.k * s * s;
+    }
+    for (unsigned long long s = t0; s <= a.mask; s += stride) {
+        if (a.table[s].key != kEmpty) {
+            long long c = a.table[s].cnt;
+            acc -= 2 * c * c;
+        }
+    }
+    block_add64(acc, &a.st->recompute);
+}
+
+}  // namespace
+
+cudaError_t launch_validate(int n, long long nnz, const long long* off, const int* col, DevState* st, cudaStream_t s)
+{
+    k_validate<<<grid_for(nnz > n ? nnz : (long long)n + 1), kSetupBlock, 0, s>>>(n, nnz, off, col, st);
+    return cudaGetLastError();
+}
+
+// lmap: 16-byte slots, lmask + 1 of them (caller-owned scratch, >= 2 k n).
+cudaError_t launch_compact_labels(int n, int k, int kp, const int* labels, int* G, void* lmap,
+                                  unsigned long long lmask, DevState* st, cudaStream_t s)
+{
+    LSlot* m = static_cast<LSlot*>(lmap);
+    const unsigned long long cap = lmask + 1;
+    k_lmap_clear<<<grid_for((long long)cap), kSetupBlock, 0, s>>>(m, cap);
+    k_label_insert<<<grid_for((long long)n * k), kSetupBlock, 0, s>>>(n, k, labels, m, lmask, st);
+    const long long tiles = ((long long)n + 31) / 32 * (((long long)kp + 31) / 32);
+    k_label_assign<<<(int)(tiles < 152 * 16 ? tiles : 152 * 16), 256, 0, s>>>(n, k, kp, labels, m, lmask, G, st);
+    k_label_sumsq<<<grid_for((long long)cap), kSetupBlock, 0, s>>>(m, cap, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(const SweepArgs& a, cudaStream_t s)
+{
+    k_init_state<<<grid_for(a.n), kSetupBlock, 0, s>>>(a.n, a.C, a.size, a.dsize, a.best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_from_ids(const SweepArgs& a, cudaStream_t s)
+{
+    k_sizes_from_ids<<<grid_for(a.n), kSetupBlock, 0, s>>>(a.n, a.C, a.size, a.dsize, a.best, a.st);
+    k_count_sizes<<<grid_for(a.n), kSetupBlock, 0, s>>>(a.n, a.C, a.size, a.st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_rebuild(const SweepArgs& a, bool conditional, cudaStream_t s)
+{
+    const int c = conditional ? 1 : 0;
+    k_table_clear<<<grid_for((long long)a.mask + 1), kSetupBlock, 0, s>>>(a.table, a.mask + 1, a.st, c);
+    k_table_reset_counters<<<1, 1, 0, s>>>(a.st, c);
+    k_table_build<<<grid_for((long long)a.n * a.k), kSetupBlock, 0, s>>>(a, c);
+    k_table_done<<<1, 1, 0, s>>>(a.st, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_recompute(const SweepArgs& a, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(&a.st->recompute, 0, sizeof(long long), s);
+    if (e != cudaSuccess) return e;
+    long long work = (long long)a.mask + 1 > a.n ? (long long)a.mask + 1 : a.n;
+    k_objective_recompute<<<grid_for(work), kSetupBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ccg

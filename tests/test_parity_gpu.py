@@ -1,0 +1,268 @@
+"""Parity of the CUDA sweep with the CPU oracle, through the C ABI.
+
+Integer arithmetic on both sides, so the bar is bit-exact: the sweep count,
+every per-sweep record (|P|, |P1|, dF of P1, fallback, moves, F), the raw
+cluster ids after each sweep, the renumbered labels and the objective.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import csr_from_edges, make_config
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def cc():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2408_11331_gb300 as m
+
+    return m
+
+
+def gpu_run(cc, row_off, col, labels, max_sweeps=20, **opt):
+    o = cc.cc_default_options()
+    for key, val in opt.items():
+        setattr(o, key, val)
+    with cc.Consensus(row_off, col, labels, o) as job:
+        sweeps = job.run_until_converged(max_sweeps)
+        return dict(sweeps=sweeps, hist=job.history(), C=job.cluster_ids(), F=job.objective(),
+                    Frec=job.objective_recompute(), labels=job.consensus_labels())
+
+
+def assert_same(g, ref):
+    assert g["sweeps"] == ref.sweeps
+    assert g["hist"] == ref.stats
+    np.testing.assert_array_equal(g["C"], ref.C)
+    assert g["F"] == ref.F == g["Frec"]
+    np.testing.assert_array_equal(g["labels"], oracle.renumber(ref.C))
+
+
+def test_sbm_full_run(cc):
+    c = make_config("sbm")
+    ref = oracle.sync_run(c["row_off"], c["col"], c["labels"], 20)
+    assert_same(gpu_run(cc, c["row_off"], c["col"], c["labels"], 20), ref)
+
+
+@pytest.mark.parametrize("n,k,seed", [(20000, 8, 11), (5003, 37, 12), (3001, 1, 13), (12000, 64, 14)])
+def test_lfr_stepwise(cc, n, k, seed):
+    """Sweep by sweep: several proposal tiles, ragged tails, k not a multiple of
+    4, k above one warp, and k = 1."""
+    c = make_config("lfr", n=n, k=k, cmin=20, cmax=min(1000, n), max_deg=min(1000, n // 4), seed=seed)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    C = oracle.singletons(n)
+    F = oracle.objective(lab, C)
+    with cc.Consensus(ro, col, lab) as job:
+        assert job.objective() == F
+        for _ in range(25):
+            r = oracle.sync_step(ro, col, lab, C, F)
+            info = job.sweep()
+            assert info == r.stats
+            np.testing.assert_array_equal(job.cluster_ids(), r.C)
+            if r.stats["proposals"] == 0:
+                break
+            C, F = r.C, r.stats["F"]
+        assert job.objective_recompute() == F
+
+
+def test_knn_small(cc):
+    c = make_config("knn", n=6000, comps=30, dim=20, k=12, seed=21)
+    ref = oracle.sync_run(c["row_off"], c["col"], c["labels"], 30)
+    assert_same(gpu_run(cc, c["row_off"], c["col"], c["labels"], 30), ref)
+
+
+def _edges(n, pairs):
+    e = np.array(pairs, dtype=np.int64).reshape(-1, 2)
+    return csr_from_edges(n, e[:, 0], e[:, 1])
+
+
+def _cases():
+    rng = np.random.default_rng(5)
+    out = {}
+    # no edges at all: one sweep, no proposal
+    out["empty"] = (np.zeros(51, np.int64), np.zeros(0, np.int32), rng.integers(0, 3, (4, 50)).astype(np.int32))
+    out["single_vertex"] = (np.zeros(2, np.int64), np.zeros(0, np.int32), np.array([[5], [7]], np.int32))
+    # star whose centre has 100 singleton neighbours (several 32-wide chunks)
+    ro, col = _edges(101, [(0, i) for i in range(1, 101)])
+    out["star"] = (ro, col, rng.integers(0, 2, (6, 101)).astype(np.int32))
+    # degrees exactly 32 and 33 around two hubs
+    pairs = [(0, i) for i in range(1, 33)] + [(40, i) for i in range(41, 74)]
+    ro, col = _edges(80, pairs)
+    out["deg32_33"] = (ro, col, rng.integers(0, 3, (5, 80)).astype(np.int32))
+    # two cliques joined by one edge, identical labels -> the cliques
+    pairs = [(i, j) for i in range(10) for j in range(i + 1, 10)] + \
+            [(i, j) for i in range(10, 25) for j in range(i + 1, 25)] + [(9, 10)]
+    ro, col = _edges(25, pairs)
+    lab = np.array([[0] * 10 + [1] * 15] * 3, np.int32)
+    out["two_cliques"] = (ro, col, lab)
+    # path with all-equal labels
+    ro, col = _edges(40, [(i, i + 1) for i in range(39)])
+    out["path"] = (ro, col, np.full((2, 40), -7, np.int32))
+    # extreme and negative label values
+    c = make_config("sbm", n=300, communities=5, k=4, seed=3)
+    lab = c["labels"].astype(np.int64) * 1_000_003 - 2 ** 31 + 5
+    lab = np.clip(lab, -2 ** 31, 2 ** 31 - 1).astype(np.int32)
+    out["extreme_labels"] = (c["row_off"], c["col"], lab)
+    # self-loops and repeated entries in the CSR
+    rows = np.repeat(np.arange(300), np.diff(c["row_off"]))
+    rows2 = np.concatenate([rows, np.arange(300), rows[:500]])
+    cols2 = np.concatenate([c["col"], np.arange(300, dtype=np.int32), c["col"][:500]])
+    order = np.lexsort((cols2, rows2))
+    ro2 = np.zeros(301, np.int64)
+    np.cumsum(np.bincount(rows2, minlength=300), out=ro2[1:])
+    out["loops_and_repeats"] = (ro2, cols2[order].astype(np.int32), c["labels"])
+    # identical partitions: the planted partition is recovered exactly
+    c = make_config("sbm", n=400, communities=8, p_in=0.3, p_out=0.01, k=1, seed=4)
+    out["identical_copies"] = (c["row_off"], c["col"], np.stack([c["truth"]] * 5).astype(np.int32))
+    return out
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_edge_cases(cc, name):
+    ro, col, lab = CASES[name]
+    ref = oracle.sync_run(ro, col, lab, 60)
+    g = gpu_run(cc, ro, col, lab, 60)
+    assert_same(g, ref)
+    if name == "identical_copies":
+        assert g["F"] == 0
+    if name in ("empty", "single_vertex"):
+        assert g["sweeps"] == 1 and g["hist"][0]["proposals"] == 0
+
+
+def test_warm_start_swap_fallback(cc):
+    """The hand-worked swap: P1 only exchanges two clusters, the matching commits one move."""
+    with open(os.path.join(GOLDEN, "swap_fallback.json")) as f:
+        g = json.load(f)
+    ro, col = _edges(g["n"], g["edges"])
+    lab = np.array(g["labels"], np.int32)
+    with cc.Consensus(ro, col, lab) as job:
+        job.set_cluster_ids(np.array(g["C0"], np.int32))
+        assert job.objective() == g["F0"]
+        info = job.sweep()
+        want = {k: v for k, v in g["sweep"].items() if k != "C"}
+        assert info == want
+        np.testing.assert_array_equal(job.cluster_ids(), g["sweep"]["C"])
+
+
+def test_warm_start_fallback_random(cc):
+    """Starts where each group is split in two halves that want to swap: the
+    fallback branch, including partial matchings, against the oracle."""
+    seen = 0
+    for seed in range(60):
+        rng = np.random.default_rng(900 + seed)
+        sizes = 2 * rng.integers(2, 6, int(rng.integers(2, 8)))
+        n = int(sizes.sum())
+        group = np.repeat(np.arange(len(sizes)), sizes)
+        k = int(rng.integers(2, 6))
+        lab = np.stack([group + 10 * i for i in range(k)]).astype(np.int32)
+        noise = rng.random(lab.shape) < 0.1
+        lab[noise] = rng.integers(0, 50, int(noise.sum()))
+        C = np.empty(n, np.int32)
+        start = 0
+        for s in sizes:
+            half = rng.permutation(np.arange(start, start + s))
+            C[half[: s // 2]] = half[0]
+            C[half[s // 2:]] = half[s // 2]
+            start += s
+        iu, ju = np.triu_indices(n, 1)
+        keep = (group[iu] == group[ju]) & (rng.random(len(iu)) < 0.8) | (rng.random(len(iu)) < 0.05)
+        ro, col = csr_from_edges(n, iu[keep], ju[keep])
+        F = oracle.objective(lab, C)
+        with cc.Consensus(ro, col, lab) as job:
+            job.set_cluster_ids(C)
+            assert job.objective() == F
+            Cs, Fs = C, F
+            for _ in range(10):
+                r = oracle.sync_step(ro, col, lab, Cs, Fs)
+                assert job.sweep() == r.stats
+                np.testing.assert_array_equal(job.cluster_ids(), r.C)
+                seen += r.stats["fallback"]
+                if r.stats["proposals"] == 0:
+                    break
+                Cs, Fs = r.C, r.stats["F"]
+    assert seen >= 3
+
+
+def test_errors_leave_state(cc):
+    c = make_config("sbm", n=200, communities=4, k=3, seed=8)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    bad = col.copy()
+    bad[5] = 200
+    with pytest.raises(cc.CCError) as e:
+        cc.Consensus(ro, bad, lab)
+    assert e.value.status == 1
+    ro_bad = ro.copy()
+    ro_bad[10] = ro_bad[11] + 1
+    with pytest.raises(cc.CCError):
+        cc.Consensus(ro_bad, col, lab)
+    with cc.Consensus(ro, col, lab) as job:
+        job.sweep()
+        before = job.cluster_ids().copy()
+        F = job.objective()
+        Cbad = before.copy()
+        Cbad[3] = -1
+        with pytest.raises(cc.CCError):
+            job.set_cluster_ids(Cbad)
+        np.testing.assert_array_equal(job.cluster_ids(), before)
+        assert job.objective() == F == job.objective_recompute()
+
+
+def test_table_full_is_reported(cc):
+    """A contingency hash far too small: bounded probing reports CC_ERR_TABLE_FULL."""
+    c = make_config("sbm", n=200, communities=4, k=3, seed=8)
+    o = cc.cc_default_options()
+    o.table_log2 = 6
+    with pytest.raises(cc.CCError) as e:
+        cc.Consensus(c["row_off"], c["col"], c["labels"], o)
+    assert e.value.status == 5
+
+
+def test_reset_and_options(cc):
+    c = make_config("lfr", n=8000, k=6, cmin=20, cmax=500, max_deg=300, seed=31)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    ref = oracle.sync_run(ro, col, lab, 20)
+    o = cc.cc_default_options()
+    o.debug_checks = 1
+    with cc.Consensus(ro, col, lab, o) as job:
+        a = job.run_until_converged(20)
+        ha, Ca = job.history(), job.cluster_ids().copy()
+        job.reset()
+        assert job.history() == []
+        b = job.run_until_converged(20)
+        assert a == b == ref.sweeps
+        assert job.history() == ha == ref.stats
+        np.testing.assert_array_equal(job.cluster_ids(), Ca)
+    # a larger table (fewer rebuilds) gives the same run
+    g = gpu_run(cc, ro, col, lab, 20, table_log2=int(np.ceil(np.log2(3 * 6 * 8000 + 64))) + 2)
+    assert_same(g, ref)
+
+
+def test_create_from_device_buffers(cc):
+    torch = pytest.importorskip("torch")
+    c = make_config("sbm", n=1000, k=10, seed=77)
+    ref = oracle.sync_run(c["row_off"], c["col"], c["labels"], 20)
+    dev = torch.device("cuda:0")
+    ro = torch.from_numpy(c["row_off"]).to(dev)
+    col = torch.from_numpy(c["col"]).to(dev)
+    lab = torch.from_numpy(np.ascontiguousarray(c["labels"])).to(dev)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    job = cc.Consensus.from_device(1000, len(c["col"]), ro.data_ptr(), col.data_ptr(), 10, lab.data_ptr(),
+                                   stream=s.cuda_stream)
+    try:
+        assert job.run_until_converged(20) == ref.sweeps
+        assert job.history() == ref.stats
+        np.testing.assert_array_equal(job.cluster_ids(), ref.C)
+    finally:
+        job.close()
