@@ -178,10 +178,10 @@ cc_status ensure_graph(cc_ctx* c, int limit, RunGraph** out)
     CC_CUDA(c, cudaStreamBeginCapture(c->own_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < limit && e == cudaSuccess; ++s) {
-        e = cudaEventRecord(g.bound[s], c->own_stream);
+        e = cudaEventRecordWithFlags(g.bound[s], c->own_stream, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_sweep(c->args, c->grid, c->own_stream, g.prop[2 * s], g.prop[2 * s + 1]);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(g.bound[limit], c->own_stream);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(g.bound[limit], c->own_stream, cudaEventRecordExternal);
     cudaError_t e2 = cudaStreamEndCapture(c->own_stream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);

@@ -483,12 +483,12 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, cudaStream_t s, cudaEvent
     const int g2 = grid;
     k_begin<<<1, 1, 0, s>>>(a.st);
     if (prop0) {
-        cudaError_t e = cudaEventRecord(prop0, s);
+        cudaError_t e = cudaEventRecordWithFlags(prop0, s, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
     k_propose<<<grid, kBlock, propose_smem_bytes(a.kp), s>>>(a);
     if (prop1) {
-        cudaError_t e = cudaEventRecord(prop1, s);
+        cudaError_t e = cudaEventRecordWithFlags(prop1, s, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
     k_stage<<<g2, kBlock, 0, s>>>(a);

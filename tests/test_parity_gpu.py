@@ -266,3 +266,18 @@ def test_create_from_device_buffers(cc):
         np.testing.assert_array_equal(job.cluster_ids(), ref.C)
     finally:
         job.close()
+
+
+def test_run_timing_and_launch_count(cc):
+    """Per-sweep device times come from events inside the run's graph; the
+    launch counter counts every kernel node of every run."""
+    c = make_config("sbm")
+    with cc.Consensus(c["row_off"], c["col"], c["labels"]) as job:
+        base = job.launch_count()
+        done = job.run_until_converged(20)
+        sweep_ms, prop_ms = job.last_run_timing()
+        assert len(sweep_ms) == len(prop_ms) == done
+        assert np.all(sweep_ms > 0) and np.all(prop_ms > 0) and np.all(prop_ms <= sweep_ms)
+        assert job.launch_count() - base == 1 + 20 * 13
+        job.sweep()
+        assert len(job.last_run_timing()[0]) == 1
