@@ -58,10 +58,24 @@ typedef struct {
                                default 20 */
     int32_t debug_checks;   /* 1: after every sweep recompute F from scratch on the device and
                                fail with CC_ERR_INVALID if it differs from the incremental F */
-    int32_t table_log2;     /* log2 of the contingency hash capacity; 0 = automatic
-                               (capacity >= 3 k n, so no sweep can fill it) */
-    int32_t reserved[5];    /* must be zero */
+    int32_t table_log2;     /* log2 of the allocated contingency hash capacity; 0 = automatic
+                               (>= 4 k n slots of 16 bytes) */
+    int32_t table_start_log2; /* log2 of the capacity in use at the singleton start; 0 =
+                               automatic (>= 2 k n).  The capacity in use then follows the
+                               live keys; a sweep that would fill it is abandoned before
+                               it commits anything and retried in twice the capacity */
+    int32_t reserved[4];    /* must be zero */
 } cc_options;
+
+/* State of the contingency hash of a context. */
+typedef struct {
+    int64_t capacity;      /* slots in use (a power of two) */
+    int64_t max_capacity;  /* slots allocated */
+    int64_t live_keys;     /* (cluster, partition, label) keys with a non-zero count */
+    int64_t used_slots;    /* occupied slots, dead keys included */
+    int64_t rebuilds;      /* rebuilds since creation (reset included) */
+    int64_t retries;       /* sweeps abandoned for lack of space and run again */
+} cc_table_info;
 
 /* Per-sweep record.  Field meanings follow the synchronous sweep of the
  * Parallel algorithm section with its validation checks fixed as:
@@ -151,6 +165,9 @@ cc_status cc_run_until_converged(cc_ctx* ctx, int32_t max_sweeps, int32_t* sweep
  * kernel.  At most max entries are written to each non-NULL array; *count
  * receives the number of sweeps that ran. */
 cc_status cc_last_run_timing(cc_ctx* ctx, int32_t max, float* sweep_ms, float* propose_ms, int32_t* count);
+
+/* Current state of the contingency hash (synchronises the stream). */
+cc_status cc_table_stats(cc_ctx* ctx, cc_table_info* out);
 
 /* Number of CUDA kernels the context has launched since creation (nodes of
  * its sweep graphs included, whether or not a stopped sweep skipped them). */

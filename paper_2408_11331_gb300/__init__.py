@@ -51,6 +51,9 @@ class Consensus:
     def last_run_timing(self):
         return _native.cc_last_run_timing(self._ctx)
 
+    def table_stats(self) -> dict:
+        return _native.cc_table_stats(self._ctx)
+
     def launch_count(self) -> int:
         return _native.cc_launch_count(self._ctx)
 

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "CC_OK", 1: "CC_ERR_INVALID", 2: "CC_ERR_OOM", 3: "CC_ERR_CUD
 
 # Every symbol include/cc.h declares; the CPU test suite checks the library exports them.
 EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", "cc_reset", "cc_set_cluster_ids", "cc_sweep",
-           "cc_run_until_converged", "cc_last_run_timing", "cc_launch_count", "cc_history", "cc_objective", "cc_objective_recompute",
+           "cc_run_until_converged", "cc_last_run_timing", "cc_table_stats", "cc_launch_count", "cc_history", "cc_objective", "cc_objective_recompute",
            "cc_consensus_labels", "cc_cluster_ids", "cc_cluster_ids_dev", "cc_last_error", "cc_destroy")
 
 
@@ -33,7 +33,16 @@ class CCError(RuntimeError):
 
 class cc_options(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
-                ("table_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("table_log2", ctypes.c_int32), ("table_start_log2", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class cc_table_info(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("max_capacity", ctypes.c_int64), ("live_keys", ctypes.c_int64),
+                ("used_slots", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("retries", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 class cc_sweep_info(ctypes.Structure):
@@ -70,6 +79,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cc_run_until_converged.argtypes = [P, c.c_int32, c.POINTER(c.c_int32)]
     lib.cc_last_run_timing.restype = c.c_int
     lib.cc_last_run_timing.argtypes = [P, c.c_int32, P, P, c.POINTER(c.c_int32)]
+    lib.cc_table_stats.restype = c.c_int
+    lib.cc_table_stats.argtypes = [P, c.POINTER(cc_table_info)]
     lib.cc_launch_count.restype = c.c_int
     lib.cc_launch_count.argtypes = [P, c.POINTER(c.c_int64)]
     lib.cc_history.restype = c.c_int
@@ -171,6 +182,12 @@ def cc_last_run_timing(ctx):
     b = np.zeros(max(count.value, 1), np.float32)
     _check(lib.cc_last_run_timing(ctx, count.value, _ptr(a), _ptr(b), ctypes.byref(count)), ctx)
     return a[: count.value], b[: count.value]
+
+
+def cc_table_stats(ctx) -> dict:
+    out = cc_table_info()
+    _check(lib.cc_table_stats(ctx, ctypes.byref(out)), ctx)
+    return out.as_dict()
 
 
 def cc_launch_count(ctx) -> int:

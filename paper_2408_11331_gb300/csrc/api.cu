@@ -39,6 +39,9 @@ struct cc_ctx {
     unsigned char* pflag = nullptr;
     unsigned int* pslot = nullptr;
     int* scratch = nullptr;             // 3n + n/1024 + 64 ints for the output renumbering
+    int* members = nullptr;             // rebuild scratch (n)
+    int* cursor = nullptr;              // rebuild scratch (n)
+    int* bsum = nullptr;                // rebuild scratch (n/1024 + 2)
     DevState* st = nullptr;
     cc_sweep_info* hist = nullptr;
     int hist_cap = 1 << 16;
@@ -48,6 +51,9 @@ struct cc_ctx {
     long long launches = 0;             // kernels launched so far
     int grid = 0;
     long long partition_sq = 0, F0 = 0;
+    unsigned long long cap_start = 0;   // active table capacity at the singleton start
+    unsigned long long cap_max = 0;     // allocated table capacity
+    bool started = false;               // start_state ran once
     cc_options opt{};
     std::vector<void*> allocs;
     std::string err;
@@ -145,9 +151,19 @@ cc_status start_state(cc_ctx* c)
 {
     DevState s;
     std::memset(&s, 0, sizeof(s));
+    if (c->started) {
+        DevState prev;
+        cc_status rp = read_state(c, &prev);
+        if (rp != CC_OK) return rp;
+        s.rebuilds = prev.rebuilds;
+        s.retries = prev.retries;
+    }
+    c->started = true;
     s.partition_sq = c->partition_sq;
     s.F = c->F0;
     s.stop = 1;
+    s.new_mask = c->cap_start - 1;
+    s.mask = c->cap_start - 1;
     CC_CUDA(c, cudaMemcpyAsync(c->st, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
     CC_CUDA(c, launch_init_state(c->args, c->stream));
     CC_CUDA(c, launch_table_rebuild(c->args, false, c->stream));
@@ -206,14 +222,21 @@ cc_status run(cc_ctx* c, int limit, int* done)
     cc_status r = ensure_graph(c, limit, &g);
     if (r != CC_OK) return r;
     CC_CUDA(c, launch_run_begin(c->st, limit, c->stream));
-    CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
-    c->launches += 1 + (long long)limit * kKernelsPerSweep;
-    c->last_limit = limit;
     DevState st;
-    r = read_state(c, &st);
-    if (r != CC_OK) return r;
+    // a sweep abandoned for lack of table space is retried in the next graph
+    // body, so a launch can end before the run does; relaunch until it stops
+    for (int launch = 0; launch < 64; ++launch) {
+        CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
+        c->launches += (long long)limit * kKernelsPerSweep;
+        r = read_state(c, &st);
+        if (r != CC_OK) return r;
+        if (st.stop || st.err) break;
+    }
+    c->launches += 1;
+    c->last_limit = limit;
     r = check_device_error(c, st);
     if (r != CC_OK) return r;
+    if (!st.stop) return fail(c, CC_ERR_TABLE_FULL, "sweep retries did not converge");
     if (done) *done = st.run_sweeps;
     if (c->opt.debug_checks) {
         long long F = 0;
@@ -240,6 +263,8 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
         for (int r : opt->reserved)
             if (r != 0) return fail(nullptr, CC_ERR_INVALID, "reserved option fields must be zero");
         if (opt->table_log2 < 0 || opt->table_log2 > 40) return fail(nullptr, CC_ERR_INVALID, "table_log2 out of range");
+        if (opt->table_start_log2 < 0 || opt->table_start_log2 > 40)
+            return fail(nullptr, CC_ERR_INVALID, "table_start_log2 out of range");
     }
 
     cc_ctx* c = new cc_ctx();
@@ -269,7 +294,7 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
     c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
 
     const unsigned long long kn = (unsigned long long)k * n;
-    unsigned long long cap = c->opt.table_log2 > 0 ? (1ull << c->opt.table_log2) : next_pow2(3 * kn + 64);
+    unsigned long long cap = c->opt.table_log2 > 0 ? (1ull << c->opt.table_log2) : next_pow2(4 * kn + 64);
     if (cap < 64) cap = 64;
 
     CC_TRY(dalloc(c, &c->off, (size_t)n + 1));
@@ -287,6 +312,9 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
     CC_TRY(dalloc(c, &c->pflag, (size_t)n));
     CC_TRY(dalloc(c, &c->pslot, 2 * (size_t)kn));
     CC_TRY(dalloc(c, &c->scratch, 3 * (size_t)n + (size_t)n / 1024 + 64));
+    CC_TRY(dalloc(c, &c->members, (size_t)n));
+    CC_TRY(dalloc(c, &c->cursor, (size_t)n));
+    CC_TRY(dalloc(c, &c->bsum, (size_t)n / 1024 + 2));
     CC_TRY(dalloc(c, &c->st, 1));
     CC_TRY(dalloc(c, &c->hist, (size_t)c->hist_cap));
 
@@ -324,6 +352,9 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
     if (s.err) return bail(fail(c, CC_ERR_INVALID, "label compaction failed"));
     c->partition_sq = s.partition_sq;
     c->F0 = c->partition_sq - (long long)k * n;
+    c->cap_start = c->opt.table_start_log2 > 0 ? (1ull << c->opt.table_start_log2) : next_pow2(2 * kn + 64);
+    if (c->cap_start > cap) c->cap_start = cap;
+    c->cap_max = cap;
 
     SweepArgs& a = c->args;
     a.n = n;
@@ -338,22 +369,17 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
     a.dsize = c->dsize;
     a.best = c->best;
     a.table = c->table;
-    a.mask = cap - 1;
-    // a sweep inserts at most 2 k n keys (staging plus matching); rebuild early enough
-    // that the next sweep cannot fill the table, and keep the load under one half
-    unsigned long long room = cap > 2 * kn ? cap - 2 * kn : 0;
-    a.thresh = room < cap / 2 ? room : cap / 2;
-    if (a.thresh < kn) {
-        // only possible with a caller-chosen table_log2; still correct, probing
-        // gives CC_ERR_TABLE_FULL instead of looping if the table ever fills
-        a.thresh = cap / 2;
-    }
+    a.mask_max = cap - 1;
+    a.cap_min = cap < 1024 ? cap : 1024;
     a.pv = c->pv;
     a.pa = c->pa;
     a.pb = c->pb;
     a.pg = c->pg;
     a.pflag = c->pflag;
     a.pslot = c->pslot;
+    a.members = c->members;
+    a.cursor = c->cursor;
+    a.bsum = c->bsum;
     a.st = c->st;
     a.hist = c->hist;
     a.hist_cap = c->hist_cap;
@@ -509,6 +535,8 @@ cc_status cc_set_cluster_ids(cc_ctx* c, const int32_t* C)
         return fail(c, CC_ERR_INVALID, "cluster ids must lie in [0, n)");
     }
     CC_CUDA(c, cudaMemcpyAsync(c->C, c->scratch, sizeof(int) * (size_t)c->n, cudaMemcpyDeviceToDevice, c->stream));
+    const unsigned long long nm = c->cap_start - 1;
+    CC_CUDA(c, cudaMemcpyAsync(&c->st->new_mask, &nm, sizeof(nm), cudaMemcpyHostToDevice, c->stream));
     CC_CUDA(c, launch_state_from_ids(c->args, c->stream));
     CC_CUDA(c, launch_table_rebuild(c->args, false, c->stream));
     c->launches += 2 + kKernelsPerRebuild;
@@ -571,6 +599,21 @@ cc_status cc_last_run_timing(cc_ctx* c, int32_t max, float* sweep_ms, float* pro
         if (sweep_ms) sweep_ms[i] = a;
         if (propose_ms) propose_ms[i] = b;
     }
+    return CC_OK;
+}
+
+cc_status cc_table_stats(cc_ctx* c, cc_table_info* out)
+{
+    if (!c || !out) return fail(c, CC_ERR_INVALID, "null argument");
+    DevState s;
+    cc_status r = read_state(c, &s);
+    if (r != CC_OK) return r;
+    out->capacity = (int64_t)(s.mask + 1);
+    out->max_capacity = (int64_t)c->cap_max;
+    out->live_keys = s.live;
+    out->used_slots = (int64_t)s.used;
+    out->rebuilds = s.rebuilds;
+    out->retries = s.retries;
     return CC_OK;
 }
 

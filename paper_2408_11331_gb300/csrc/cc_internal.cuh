@@ -9,7 +9,11 @@
 //   C     int32[n]     cluster id of each vertex (founding-vertex ids)
 //   size  int32[n]     cluster sizes, indexed by cluster id
 //   table Slot[cap]    the contingency counts n(c, i, l) as an open-addressing
-//                      hash with linear probing, key = c << 32 | g, cap = 2^p.
+//                      hash with linear probing, key = c << 32 | g.  The buffer holds
+//                      2^p >= 3 k n slots; only an active prefix of 2^q slots is used
+//                      (st->mask = 2^q - 1), grown before a sweep stages its moves and
+//                      shrunk when few keys are live, so that the probes of late
+//                      sweeps stay in L2.
 #pragma once
 
 #include <cstdint>
@@ -43,9 +47,15 @@ struct DevState {
     unsigned long long used;     // occupied table slots
     long long live;              // keys with a non-zero count
     unsigned long long tile_ctr; // next vertex tile of the proposal kernel
+    unsigned long long mask;     // active table capacity - 1 (a power of two minus one)
+    unsigned long long new_mask; // capacity - 1 of a pending rebuild
     long long partition_sq;      // sum_i sum_j |P_ij|^2
     long long recompute;         // output of the full objective reduction
     int mode;                    // 0 nothing to commit, 1 commit P1, 2 matching
+    int overflow;                // 1: the table ran short during this sweep (nothing committed)
+    int abort;                   // 1: the pending rebuild follows an abandoned sweep
+    int retries;                 // sweeps abandoned and retried in a larger table
+    int rebuilds;                // table rebuilds since creation
     int skip;                    // 1: this sweep does nothing (the run has stopped)
     int stop;                    // 1: the run has stopped
     int rebuild;                 // 1: a table rebuild is pending
@@ -67,14 +77,17 @@ struct SweepArgs {
     int* dsize;                 // staged size deltas
     unsigned long long* best;   // matching keys per cluster
     Slot* table;
-    unsigned long long mask;    // cap - 1
-    unsigned long long thresh;  // rebuild when used slots exceed this
+    unsigned long long mask_max; // allocated capacity - 1; the active capacity is st->mask + 1
+    unsigned long long cap_min;  // smallest active capacity
     int* pv;                    // proposal list: vertex,
     int* pa;                    //   source cluster,
     int* pb;                    //   target cluster,
     int* pg;                    //   gain dD
     unsigned char* pflag;       //   1 if kept by the singleton guard
     unsigned int* pslot;        //   table slots of (a, g_i(v)) and (b, g_i(v)), 2 per (j, i)
+    int* members;               // rebuild scratch: vertices listed cluster by cluster (n)
+    int* cursor;                // rebuild scratch: next free position of each cluster (n)
+    int* bsum;                  // rebuild scratch: per-block sums of the size scan (n / 1024 + 1)
     DevState* st;
     cc_sweep_info* hist;
     int hist_cap;
@@ -155,14 +168,16 @@ cudaError_t launch_compact_labels(int n, int k, int kp, const int* labels, int* 
                                   unsigned long long lmask, DevState* st, cudaStream_t s);
 cudaError_t launch_init_state(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_state_from_ids(const SweepArgs& a, cudaStream_t s);
+// Rebuild of the table from C into st->new_mask + 1 slots, then st->mask = st->new_mask.
+// conditional: only if st->rebuild is set (decided on the device).
 cudaError_t launch_table_rebuild(const SweepArgs& a, bool conditional, cudaStream_t s);
 cudaError_t launch_objective_recompute(const SweepArgs& a, cudaStream_t s);
 
 // ---- launch wrappers (sweep.cu) ----
 cudaError_t launch_run_begin(DevState* st, int limit, cudaStream_t s);
 // One sweep (13 kernels); prop0/prop1 (may be null) are recorded around the proposal kernel.
-constexpr int kKernelsPerSweep = 13;
-constexpr int kKernelsPerRebuild = 4;
+constexpr int kKernelsPerRebuild = 8;
+constexpr int kKernelsPerSweep = 10 + kKernelsPerRebuild;
 cudaError_t launch_sweep(const SweepArgs& a, int grid, cudaStream_t s, cudaEvent_t prop0, cudaEvent_t prop1);
 size_t propose_smem_bytes(int kp);
 cudaError_t prepare_propose(int kp, int* blocks_per_sm);

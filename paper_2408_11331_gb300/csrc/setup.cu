@@ -185,48 +185,159 @@ __global__ void k_count_sizes(int n, const int* __restrict__ C, int* size, DevSt
     }
 }
 
-__global__ void k_table_clear(Slot* t, unsigned long long cap, const DevState* st, int conditional)
+// ---- table rebuild ------------------------------------------------------
+// The table is rebuilt from C alone: clear the capacity being built, list the
+// vertices cluster by cluster (counting sort: an exclusive scan of the sizes
+// gives each cluster's first position), then insert the keys with partitions
+// innermost per member, so that the 32 lanes of a warp hold consecutive
+// members of (mostly) one cluster for one partition: equal keys are merged
+// with __match_any_sync and added with one atomic.  All kernels are skipped
+// unless a rebuild is pending (conditional) and run unconditionally at reset.
+
+__device__ __forceinline__ bool rebuild_off(const DevState* st, int conditional)
 {
-    if (conditional && (!st->rebuild || st->err)) return;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += stride)
-        reinterpret_cast<ulonglong2*>(t)[s] = make_ulonglong2(kEmpty, 0ull);
+    return conditional && (!st->rebuild || st->err);
 }
 
-// Inserts (C[v], g_i(v)) with count +1 for every (v, i); counts new slots.
-__global__ void k_table_build(SweepArgs a, int conditional)
+// Clears the slots of the capacity being built (st->new_mask + 1 of them), and
+// the staged size deltas after an abandoned sweep.
+__global__ void k_table_clear(Slot* t, int* dsize, int n, const DevState* st, int conditional)
 {
-    DevState* st = a.st;
-    if (conditional && (!st->rebuild || st->err)) return;
-    const long long total = (long long)a.n * a.k;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-        const long long t = base + threadIdx.x;
-        bool ins = false;
-        if (t < total) {
-            const int v = (int)(t / a.k), i = (int)(t - (long long)v * a.k);
-            const unsigned long long key = ckey(a.C[v], a.G[(long long)v * a.kp + i]);
-            long long s = table_find_or_insert(a.table, a.mask, key, &ins);
-            if (s < 0) set_err(st, CC_ERR_TABLE_FULL);
-            else atomicAdd(&a.table[s].cnt, 1);
-        }
-        unsigned m = __ballot_sync(0xffffffffu, ins);
-        if (lane == 0 && m) atomicAdd(&st->used, (unsigned long long)__popc(m));
-    }
+    if (rebuild_off(st, conditional)) return;
+    const unsigned long long cap = st->new_mask + 1;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (unsigned long long s = t0; s < cap; s += stride)
+        reinterpret_cast<ulonglong2*>(t)[s] = make_ulonglong2(kEmpty, 0ull);
+    if (st->abort)
+        for (unsigned long long v = t0; v < (unsigned long long)n; v += stride) dsize[v] = 0;
 }
 
 __global__ void k_table_reset_counters(DevState* st, int conditional)
 {
-    if (conditional && (!st->rebuild || st->err)) return;
+    if (rebuild_off(st, conditional)) return;
     st->used = 0;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Block sums of size[] over blocks of 1024 entries.
+__global__ void __launch_bounds__(1024) k_scan_blocks(const int* __restrict__ in, int n, int* bsum,
+                                                      const DevState* st, int conditional)
+{
+    if (rebuild_off(st, conditional)) return;
+    __shared__ int wsum[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = i < n ? in[i] : 0;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int y = wsum[lane];
+        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+        if (lane == 0) bsum[blockIdx.x] = y;
+    }
+}
+
+// Exclusive scan of the nb block sums in place (one block, 1024 threads, each
+// owning a contiguous run).
+__global__ void __launch_bounds__(1024) k_scan_sums(int nb, int* bsum, const DevState* st, int conditional)
+{
+    if (rebuild_off(st, conditional)) return;
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int per = (nb + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+    int sum = 0;
+    for (int b = lo; b < hi; ++b) sum += bsum[b];
+    int x = warp_incl_scan(sum, lane);
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) wsum[lane] = warp_incl_scan(wsum[lane], lane);
+    __syncthreads();
+    int run = x - sum + (w > 0 ? wsum[w - 1] : 0);
+    for (int b = lo; b < hi; ++b) {
+        const int y = bsum[b];
+        bsum[b] = run;
+        run += y;
+    }
+}
+
+// cursor[c] = exclusive prefix of size[] (the first position of cluster c).
+__global__ void __launch_bounds__(1024) k_scan_write(const int* __restrict__ in, int n, const int* __restrict__ bsum,
+                                                     int* out, const DevState* st, int conditional)
+{
+    if (rebuild_off(st, conditional)) return;
+    __shared__ int wsum[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = i < n ? in[i] : 0;
+    int x = warp_incl_scan(v, lane);
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) wsum[lane] = warp_incl_scan(wsum[lane], lane);
+    __syncthreads();
+    if (i < n) out[i] = bsum[blockIdx.x] + x - v + (w > 0 ? wsum[w - 1] : 0);
+}
+
+__global__ void k_members_scatter(int n, const int* __restrict__ C, int* cursor, int* members, const DevState* st,
+                                  int conditional)
+{
+    if (rebuild_off(st, conditional)) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int pos = atomicAdd(&cursor[C[v]], 1);
+        if (pos < n) members[pos] = (int)v;
+        else set_err(const_cast<DevState*>(st), CC_ERR_INVALID);  // sizes inconsistent with C
+    }
+}
+
+__global__ void k_table_build(SweepArgs a, int conditional)
+{
+    DevState* st = a.st;
+    if (rebuild_off(st, conditional)) return;
+    const unsigned long long mask = st->new_mask;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+        const long long m = base + threadIdx.x;
+        const bool valid = m < a.n;
+        int v = 0, c = 0;
+        if (valid) {
+            v = a.members[m];
+            c = a.C[v];
+        }
+        const int* row = a.G + (long long)v * a.kp;
+        for (int i = 0; i < a.k; ++i) {
+            const unsigned long long key = valid ? ckey(c, row[i]) : kEmpty;
+            const unsigned same = __match_any_sync(0xffffffffu, key);
+            bool ins = false;
+            if (valid && (__ffs(same) - 1) == lane) {
+                const long long s = table_find_or_insert(a.table, mask, key, &ins);
+                if (s < 0) set_err(st, CC_ERR_TABLE_FULL);
+                else atomicAdd(&a.table[s].cnt, __popc(same));
+            }
+            const unsigned mi = __ballot_sync(0xffffffffu, ins);
+            if (lane == 0 && mi) atomicAdd(&st->used, (unsigned long long)__popc(mi));
+        }
+    }
 }
 
 __global__ void k_table_done(DevState* st, int conditional)
 {
-    if (conditional && (!st->rebuild || st->err)) return;
+    if (rebuild_off(st, conditional)) return;
     st->live = (long long)st->used;
+    st->mask = st->new_mask;
     st->rebuild = 0;
+    st->abort = 0;
+    st->rebuilds += 1;
 }
 
 __global__ void k_objective_recompute(SweepArgs a)
@@ -238,7 +349,8 @@ __global__ void k_objective_recompute(SweepArgs a)
         long long s = a.size[v];
         acc += (long long)a.k * s * s;
     }
-    for (unsigned long long s = t0; s <= a.mask; s += stride) {
+    const unsigned long long mask = a.st->mask;
+    for (unsigned long long s = t0; s <= mask; s += stride) {
         if (a.table[s].key != kEmpty) {
             long long c = a.table[s].cnt;
             acc -= 2 * c * c;
@@ -285,9 +397,14 @@ cudaError_t launch_state_from_ids(const SweepArgs& a, cudaStream_t s)
 cudaError_t launch_table_rebuild(const SweepArgs& a, bool conditional, cudaStream_t s)
 {
     const int c = conditional ? 1 : 0;
-    k_table_clear<<<grid_for((long long)a.mask + 1), kSetupBlock, 0, s>>>(a.table, a.mask + 1, a.st, c);
+    const int nb = (a.n + 1023) / 1024;
+    k_table_clear<<<grid_for((long long)a.mask_max + 1), kSetupBlock, 0, s>>>(a.table, a.dsize, a.n, a.st, c);
     k_table_reset_counters<<<1, 1, 0, s>>>(a.st, c);
-    k_table_build<<<grid_for((long long)a.n * a.k), kSetupBlock, 0, s>>>(a, c);
+    k_scan_blocks<<<nb, 1024, 0, s>>>(a.size, a.n, a.bsum, a.st, c);
+    k_scan_sums<<<1, 1024, 0, s>>>(nb, a.bsum, a.st, c);
+    k_scan_write<<<nb, 1024, 0, s>>>(a.size, a.n, a.bsum, a.cursor, a.st, c);
+    k_members_scatter<<<grid_for(a.n), kSetupBlock, 0, s>>>(a.n, a.C, a.cursor, a.members, a.st, c);
+    k_table_build<<<grid_for(a.n), kSetupBlock, 0, s>>>(a, c);
     k_table_done<<<1, 1, 0, s>>>(a.st, c);
     return cudaGetLastError();
 }
@@ -296,7 +413,7 @@ cudaError_t launch_objective_recompute(const SweepArgs& a, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(&a.st->recompute, 0, sizeof(long long), s);
     if (e != cudaSuccess) return e;
-    long long work = (long long)a.mask + 1 > a.n ? (long long)a.mask + 1 : a.n;
+    long long work = (long long)a.mask_max + 1 > a.n ? (long long)a.mask_max + 1 : a.n;
     k_objective_recompute<<<grid_for(work), kSetupBlock, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -82,43 +82,6 @@ __device__ __forceinline__ int resolve(const Slot* t, unsigned long long mask, u
     return 0;
 }
 
-// A_x = sum_i n(x, g_i(v)) by k probes, four first loads in flight at a time.
-__device__ __forceinline__ int agree_table(const Slot* __restrict__ t, unsigned long long mask, int x,
-                                           const int* sg, int k)
-{
-    int A = 0;
-    int i = 0;
-    for (; i + 4 <= k; i += 4) {
-        const unsigned long long k0 = ckey(x, sg[i]), k1 = ckey(x, sg[i + 1]);
-        const unsigned long long k2 = ckey(x, sg[i + 2]), k3 = ckey(x, sg[i + 3]);
-        const unsigned long long h0 = mix64(k0) & mask, h1 = mix64(k1) & mask;
-        const unsigned long long h2 = mix64(k2) & mask, h3 = mix64(k3) & mask;
-        const ulonglong2 e0 = __ldg(reinterpret_cast<const ulonglong2*>(t + h0));
-        const ulonglong2 e1 = __ldg(reinterpret_cast<const ulonglong2*>(t + h1));
-        const ulonglong2 e2 = __ldg(reinterpret_cast<const ulonglong2*>(t + h2));
-        const ulonglong2 e3 = __ldg(reinterpret_cast<const ulonglong2*>(t + h3));
-        A += resolve(t, mask, k0, h0, e0) + resolve(t, mask, k1, h1, e1) + resolve(t, mask, k2, h2, e2) +
-             resolve(t, mask, k3, h3, e3);
-    }
-    for (; i < k; ++i) A += table_count_ro(t, mask, ckey(x, sg[i]));
-    return A;
-}
-
-// Partitions in which u agrees with v: u's label row (16-byte aligned, kp
-// entries, padding -1) against v's row in shared memory (padding -2).
-__device__ __forceinline__ int agree_row(const int* __restrict__ gu, const int* sg, int kp)
-{
-    const int4* g4 = reinterpret_cast<const int4*>(gu);
-    const int4* s4 = reinterpret_cast<const int4*>(sg);
-    int A = 0;
-    for (int q = 0; q < (kp >> 2); ++q) {
-        const int4 a = __ldg(g4 + q);
-        const int4 b = s4[q];
-        A += (a.x == b.x) + (a.y == b.y) + (a.z == b.z) + (a.w == b.w);
-    }
-    return A;
-}
-
 __global__ void k_run_begin(DevState* st, int limit)
 {
     st->stop = 0;
@@ -129,6 +92,7 @@ __global__ void k_run_begin(DevState* st, int limit)
 __global__ void k_begin(DevState* st)
 {
     st->skip = (st->stop || st->err) ? 1 : 0;
+    st->overflow = 0;
     st->nprop = 0;
     st->np1 = 0;
     st->dF = 0;
@@ -138,25 +102,101 @@ __global__ void k_begin(DevState* st)
     st->mode = 0;
 }
 
-// Warp per vertex; each lane takes one neighbour of a 32-wide chunk, equal
-// candidate clusters inside the chunk are merged with __match_any_sync, and
-// every distinct candidate is scored by the lane that holds it.  Blocks claim
-// tiles of kTile vertices and their warps claim single vertices from the
-// tile, which balances skewed degrees; proposals are gathered per tile in
-// shared memory and appended with one global atomic.
+// Per-warp scratch of the proposal kernel (shared memory).
+struct WarpScratch {
+    int cx[33];    // entries to score: the own cluster (entry 0, when not a singleton), then
+    int cu[33];    // the distinct candidate clusters of the chunk, a neighbour carrying each
+    int cs[33];    // (the only member for a singleton), and their sizes
+    int seen[128]; // candidates already scored for this vertex (degree > 32 only)
+};
+
+constexpr int kInflight = 4;  // table probes per lane issued before the first is resolved
+
+// Agreement A_x = sum_i n(x, g_i(v)) of the entry held by this lane's group:
+// the warp is split into groups of gs lanes (gs = 32 / next_pow2(entries)), one
+// entry per group; the lanes of a group share the partitions.  A singleton {u}
+// is scored from u's label row against v's (int4 loads), any other cluster by
+// hash probes with kInflight first loads in flight per lane.  The group's
+// lanes are summed with xor shuffles (groups are aligned, so they stay apart).
+__device__ __forceinline__ int score_entry(const SweepArgs& a, const Slot* __restrict__ table,
+                                           unsigned long long mask, const int* sg, int x, int u, int sx,
+                                           bool valid, int l, int gs)
+{
+    int acc = 0;
+    if (valid) {
+        if (sx == 1) {
+            const int4* g4 = reinterpret_cast<const int4*>(a.G + (long long)u * a.kp);
+            const int4* s4 = reinterpret_cast<const int4*>(sg);
+            const int kq = a.kp >> 2;
+            for (int q0 = l; q0 < kq; q0 += gs * 8) {
+                int4 r[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const int q = q0 + b * gs;
+                    r[b] = q < kq ? __ldg(g4 + q) : make_int4(-1, -1, -1, -1);
+                }
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const int q = q0 + b * gs;
+                    if (q < kq) {
+                        const int4 s = s4[q];
+                        acc += (r[b].x == s.x) + (r[b].y == s.y) + (r[b].z == s.z) + (r[b].w == s.w);
+                    }
+                }
+            }
+        } else {
+            for (int i0 = l; i0 < a.k; i0 += gs * kInflight) {
+                unsigned long long key[kInflight], h[kInflight];
+                ulonglong2 ev[kInflight];
+#pragma unroll
+                for (int b = 0; b < kInflight; ++b) {
+                    const int i = i0 + b * gs;
+                    key[b] = 0;
+                    h[b] = 0;
+                    ev[b] = make_ulonglong2(kEmpty, 0ull);
+                    if (i < a.k) {
+                        key[b] = ckey(x, sg[i]);
+                        h[b] = mix64(key[b]) & mask;
+                        ev[b] = __ldg(reinterpret_cast<const ulonglong2*>(table + h[b]));
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < kInflight; ++b)
+                    if (i0 + b * gs < a.k) acc += resolve(table, mask, key[b], h[b], ev[b]);
+            }
+        }
+    }
+    for (int o = gs >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    return acc;
+}
+
+// Warp per vertex.  Each chunk of 32 neighbours: the lane holding a neighbour
+// reads its cluster; equal clusters are merged with __match_any_sync (and,
+// past the first chunk, with a per-warp seen-set) and the distinct candidates
+// are compacted into shared memory, after the vertex's own cluster in the
+// first chunk.  The warp then scores all entries at once, one group of lanes
+// per entry (score_entry), and keeps the least packed (dD, id).  Blocks claim
+// 256-vertex tiles and warps claim single vertices from their tile, which
+// balances skewed degrees; proposals are gathered per tile in shared memory
+// and appended with one global atomic per tile.
 __global__ void __launch_bounds__(kBlock) k_propose(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip) return;
+    const unsigned long long mask = st->mask;
     extern __shared__ int4 smem4[];
-    int4* sbuf = smem4;                                   // kTile proposals
-    int* sG = reinterpret_cast<int*>(smem4 + kTile);       // own label row per warp
+    int4* sbuf = smem4;                                            // kTile proposals
+    WarpScratch* wsall = reinterpret_cast<WarpScratch*>(smem4 + kTile);
+    int* sG = reinterpret_cast<int*>(wsall + kWarpsPerBlock);      // own label row per warp
     __shared__ long long s_tile;
     __shared__ int s_next, s_cnt;
     __shared__ unsigned long long s_gbase;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    WarpScratch& ws = wsall[w];
     int* sg = sG + w * a.kp;
     const int k = a.k;
+    const Slot* __restrict__ table = a.table;
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -174,19 +214,18 @@ __global__ void __launch_bounds__(kBlock) k_propose(SweepArgs a)
             idx = __shfl_sync(kFull, idx, 0);
             if (idx >= tlen) break;
             const int v = (int)(tile + idx);
+            const long long beg = __ldg(a.off + v), end = __ldg(a.off + v + 1);
+            if (beg == end) continue;  // isolated: never moves
             const int cv = __ldg(a.C + v);
             const int sa = __ldg(a.size + cv);
             const int* gv = a.G + (long long)v * a.kp;
             for (int i = lane; i < a.kp; i += 32) sg[i] = i < k ? __ldg(gv + i) : -2;
+            const bool use_seen = end - beg > 32;
+            if (use_seen)
+                for (int q = lane; q < 128; q += 32) ws.seen[q] = -1;
             __syncwarp();
-            int Aa = k;
-            if (sa > 1) {
-                int part = 0;
-                for (int i = lane; i < k; i += 32) part += table_count_ro(a.table, a.mask, ckey(cv, sg[i]));
-                Aa = __reduce_add_sync(kFull, part);
-            }
+            int Aa = k;  // A_a = sum_i n(a, g_i(v)); k for a singleton
             unsigned long long best = kEmpty;
-            const long long beg = __ldg(a.off + v), end = __ldg(a.off + v + 1);
             for (long long base = beg; base < end; base += 32) {
                 const long long e = base + lane;
                 int u = -1, x = -1;
@@ -198,14 +237,47 @@ __global__ void __launch_bounds__(kBlock) k_propose(SweepArgs a)
                     }
                 }
                 const unsigned m = __match_any_sync(kFull, x);
-                if (x >= 0 && (__ffs(m) - 1) == lane) {
-                    const int sx = __ldg(a.size + x);
-                    const int Ax = sx == 1 ? agree_row(a.G + (long long)u * a.kp, sg, a.kp)
-                                           : agree_table(a.table, a.mask, x, sg, k);
-                    const int dD = 2 * (Aa - k - Ax) - k * (sa - 1 - sx);
-                    const unsigned long long key = pack_key(dD, x);
-                    best = key < best ? key : best;
+                bool lead = x >= 0 && (__ffs(m) - 1) == lane;
+                if (use_seen && lead) {
+                    unsigned h = ((unsigned)x * 2654435761u) >> 25;
+                    for (int t = 0; t < 128; ++t, h = (h + 1) & 127) {
+                        const int old = atomicCAS(&ws.seen[h], -1, x);
+                        if (old == -1) break;
+                        if (old == x) { lead = false; break; }
+                    }
                 }
+                const bool own = base == beg && sa > 1;  // the own cluster is scored with the first chunk
+                const int e0 = own ? 1 : 0;
+                const unsigned lb = __ballot_sync(kFull, lead);
+                const int ne = e0 + __popc(lb);
+                if (lane == 0 && own) {
+                    ws.cx[0] = cv;
+                    ws.cu[0] = v;
+                    ws.cs[0] = sa;
+                }
+                if (lead) {
+                    const int p = e0 + __popc(lb & lt);
+                    ws.cx[p] = x;
+                    ws.cu[p] = u;
+                    ws.cs[p] = __ldg(a.size + x);
+                }
+                __syncwarp();
+                // groups of gs lanes, 32 / gs >= entries (33 entries: two passes of 32)
+                for (int p0 = 0; p0 < ne; p0 += 32) {
+                    const int cnt = min(32, ne - p0);
+                    const int gs = cnt > 16 ? 1 : cnt > 8 ? 2 : cnt > 4 ? 4 : cnt > 2 ? 8 : cnt > 1 ? 16 : 32;
+                    const int j = p0 + lane / gs, l = lane & (gs - 1);
+                    const bool valid = j < ne;
+                    const int xj = valid ? ws.cx[j] : 0, uj = valid ? ws.cu[j] : 0, sj = valid ? ws.cs[j] : 0;
+                    const int A = score_entry(a, table, mask, sg, xj, uj, sj, valid, l, gs);
+                    if (own && p0 == 0) Aa = __shfl_sync(kFull, A, 0);
+                    if (valid && l == 0 && !(own && j == 0)) {
+                        const int dD = 2 * (Aa - k - A) - k * (sa - 1 - sj);
+                        const unsigned long long kk = pack_key(dD, xj);
+                        best = kk < best ? kk : best;
+                    }
+                }
+                __syncwarp();
             }
             best = warp_min64(best);
             if (lane == 0 && best != kEmpty && key_gain(best) < 0) {
@@ -229,11 +301,29 @@ __global__ void __launch_bounds__(kBlock) k_propose(SweepArgs a)
     }
 }
 
-// One thread per (proposal j, partition i).
+// Occupancy above which a sweep is abandoned and retried in a larger table.
+__device__ __forceinline__ unsigned long long fill_limit(unsigned long long mask)
+{
+    return (mask + 1) - ((mask + 1) >> 3);
+}
+
+// Adds the warp's new slots to st->used and flags an overflow past the limit.
+__device__ __forceinline__ void count_inserts(DevState* st, unsigned mi, unsigned long long mask)
+{
+    if (mi) {
+        const unsigned long long old = atomicAdd(&st->used, (unsigned long long)__popc(mi));
+        if (old + __popc(mi) > fill_limit(mask)) st->overflow = 1;
+    }
+}
+
+// One thread per (proposal j, partition i).  Staging never fails: if the
+// table runs short of slots the sweep is abandoned (st->overflow) before
+// anything is committed, and k_end schedules a larger table and a retry.
 __global__ void k_stage(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip || st->err) return;
+    const unsigned long long mask = st->mask;
     const long long total = (long long)st->nprop * a.k;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
@@ -255,12 +345,12 @@ __global__ void k_stage(SweepArgs a)
             }
             if (keep) {
                 const int g = a.G[(long long)v * a.kp + i];
-                const long long sa = table_find(a.table, a.mask, ckey(ca, g));
-                const long long sb = table_find_or_insert(a.table, a.mask, ckey(cb, g), &ins);
+                const long long sa = table_find(a.table, mask, ckey(ca, g));
+                const long long sb = table_find_or_insert(a.table, mask, ckey(cb, g), &ins);
                 if (sa < 0) {
                     set_err(st, CC_ERR_INVALID);  // the vertex's own key must exist
                 } else if (sb < 0) {
-                    set_err(st, CC_ERR_TABLE_FULL);
+                    st->overflow = 1;
                 } else {
                     atomicAdd(&a.table[sa].dlt, -1);
                     atomicAdd(&a.table[sb].dlt, 1);
@@ -271,7 +361,7 @@ __global__ void k_stage(SweepArgs a)
         }
         const unsigned mi = __ballot_sync(kFull, ins), mh = __ballot_sync(kFull, head);
         if (lane == 0) {
-            if (mi) atomicAdd(&st->used, (unsigned long long)__popc(mi));
+            count_inserts(st, mi, mask);
             if (mh) atomicAdd(&st->np1, (unsigned long long)__popc(mh));
         }
     }
@@ -283,7 +373,7 @@ __global__ void k_stage(SweepArgs a)
 __global__ void k_eval(SweepArgs a)
 {
     DevState* st = a.st;
-    if (st->skip || st->err) return;
+    if (st->skip || st->err || st->overflow) return;
     const long long total = (long long)st->nprop * a.k;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
@@ -311,7 +401,7 @@ __global__ void k_eval(SweepArgs a)
 __global__ void k_decide(DevState* st)
 {
     if (st->skip) return;
-    if (st->err) {
+    if (st->err || st->overflow) {
         st->mode = 0;
         return;
     }
@@ -386,37 +476,70 @@ __global__ void k_commit(SweepArgs a)
 
 // Fallback: a proposal is committed iff its (dD, v) is the least at both of
 // its clusters; the committed moves touch pairwise-disjoint clusters, so
-// their objective changes add exactly.
-__global__ void k_match_commit(SweepArgs a)
+// their objective changes add exactly.  Phase 1 (thread per (proposal,
+// partition)) marks the winners and inserts their target keys, so that an
+// overflow is seen before any count changes; phase 2 applies the moves.
+__global__ void k_match_keys(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip || st->err || st->mode != 2) return;
-    const long long np = (long long)st->nprop;
+    const unsigned long long mask = st->mask;
+    const long long total = (long long)st->nprop * a.k;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
-        const int v = a.pv[j], ca = a.pa[j], cb = a.pb[j], g = a.pg[j];
-        const unsigned long long key = pack_key(g, v);
-        if (a.best[ca] != key || a.best[cb] != key) continue;
-        a.C[v] = cb;
-        atomicAdd(&a.size[ca], -1);
-        atomicAdd(&a.size[cb], 1);
-        long long live = 0;
-        unsigned long long used = 0;
-        for (int i = 0; i < a.k; ++i) {
-            const int gg = a.G[(long long)v * a.kp + i];
-            const long long sa = table_find(a.table, a.mask, ckey(ca, gg));
-            bool ins = false;
-            const long long sb = table_find_or_insert(a.table, a.mask, ckey(cb, gg), &ins);
-            if (sa < 0) { set_err(st, CC_ERR_INVALID); continue; }
-            if (sb < 0) { set_err(st, CC_ERR_TABLE_FULL); continue; }
-            used += ins;
-            if (atomicAdd(&a.table[sa].cnt, -1) == 1) --live;
-            if (atomicAdd(&a.table[sb].cnt, 1) == 0) ++live;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
+        const long long t = base + threadIdx.x;
+        bool ins = false;
+        if (t < total) {
+            const long long j = t / a.k;
+            const int i = (int)(t - j * a.k);
+            const int v = a.pv[j], ca = a.pa[j], cb = a.pb[j];
+            const unsigned long long key = pack_key(a.pg[j], v);
+            if (a.best[ca] == key && a.best[cb] == key) {
+                if (i == 0) a.pflag[j] = 2;
+                const long long sb = table_find_or_insert(a.table, mask, ckey(cb, a.G[(long long)v * a.kp + i]), &ins);
+                if (sb < 0) st->overflow = 1;
+            }
         }
-        if (live) atomicAdd(reinterpret_cast<unsigned long long*>(&st->live), (unsigned long long)live);
-        if (used) atomicAdd(&st->used, used);
-        atomicAdd(&st->moves, 1ull);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&st->dF), (unsigned long long)(2LL * g));
+        const unsigned mi = __ballot_sync(kFull, ins);
+        if (lane == 0) count_inserts(st, mi, mask);
+    }
+}
+
+__global__ void k_match_apply(SweepArgs a)
+{
+    DevState* st = a.st;
+    if (st->skip || st->err || st->overflow || st->mode != 2) return;
+    const unsigned long long mask = st->mask;
+    const long long total = (long long)st->nprop * a.k;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
+        const long long t = base + threadIdx.x;
+        long long live = 0;
+        if (t < total) {
+            const long long j = t / a.k;
+            const int i = (int)(t - j * a.k);
+            if (a.pflag[j] == 2) {
+                const int v = a.pv[j], ca = a.pa[j], cb = a.pb[j];
+                if (i == 0) {
+                    a.C[v] = cb;
+                    atomicAdd(&a.size[ca], -1);
+                    atomicAdd(&a.size[cb], 1);
+                    atomicAdd(&st->moves, 1ull);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&st->dF), (unsigned long long)(2LL * a.pg[j]));
+                }
+                const int g = a.G[(long long)v * a.kp + i];
+                const long long sa = table_find(a.table, mask, ckey(ca, g));
+                const long long sb = table_find(a.table, mask, ckey(cb, g));
+                if (sa < 0 || sb < 0) {
+                    set_err(st, CC_ERR_INVALID);
+                } else {
+                    if (atomicAdd(&a.table[sa].cnt, -1) == 1) --live;
+                    if (atomicAdd(&a.table[sb].cnt, 1) == 0) ++live;
+                }
+            }
+        }
+        block_add64(live, &st->live);
     }
 }
 
@@ -440,6 +563,21 @@ __global__ void k_end(SweepArgs a)
         st->stop = 1;
         return;
     }
+    const unsigned long long cap = st->mask + 1;
+    if (st->overflow) {
+        // nothing was committed: retry this sweep after rebuilding into twice
+        // the capacity (the staged deltas are discarded with the old table)
+        if (cap >= a.mask_max + 1) {
+            set_err(st, CC_ERR_TABLE_FULL);
+            st->stop = 1;
+            return;
+        }
+        st->new_mask = 2 * cap - 1;
+        st->abort = 1;
+        st->rebuild = 1;
+        st->retries += 1;
+        return;
+    }
     if (st->mode != 0) st->F += st->dF;
     if (st->sweeps < a.hist_cap) {
         cc_sweep_info r;
@@ -454,14 +592,27 @@ __global__ void k_end(SweepArgs a)
     st->sweeps += 1;
     st->run_sweeps += 1;
     if (st->nprop == 0 || st->run_sweeps >= st->run_limit) st->stop = 1;
-    st->rebuild = st->used > a.thresh ? 1 : 0;
+    // compaction: rebuild when occupied slots pass one half (dead keys), or
+    // shrink when the live keys fill less than one sixth of the capacity.  The
+    // new capacity holds the live keys plus half of k x (moves of this sweep),
+    // a forecast of the next sweep's new keys, at load <= 1/2.
+    const unsigned long long live = (unsigned long long)st->live;
+    const unsigned long long want = 2 * live + (unsigned long long)a.k * st->moves;
+    unsigned long long c = a.cap_min;
+    while (c < want && c < a.mask_max + 1) c <<= 1;
+    if (st->used > cap / 2 || (live * 6 < cap && c < cap)) {
+        st->new_mask = c - 1;
+        st->rebuild = 1;
+    } else {
+        st->rebuild = 0;
+    }
 }
 
 }  // namespace
 
 size_t propose_smem_bytes(int kp)
 {
-    return sizeof(int4) * kTile + sizeof(int) * (size_t)kWarpsPerBlock * kp;
+    return sizeof(int4) * kTile + sizeof(WarpScratch) * kWarpsPerBlock + sizeof(int) * (size_t)kWarpsPerBlock * kp;
 }
 
 cudaError_t prepare_propose(int kp, int* blocks_per_sm)
@@ -495,7 +646,8 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, cudaStream_t s, cudaEvent
     k_eval<<<g2, kBlock, 0, s>>>(a);
     k_decide<<<1, 1, 0, s>>>(a.st);
     k_commit<<<g2, kBlock, 0, s>>>(a);
-    k_match_commit<<<g2, kBlock, 0, s>>>(a);
+    k_match_keys<<<g2, kBlock, 0, s>>>(a);
+    k_match_apply<<<g2, kBlock, 0, s>>>(a);
     k_match_reset<<<g2, kBlock, 0, s>>>(a);
     k_end<<<1, 1, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();

@@ -42,8 +42,8 @@ def test_exports_every_declared_symbol(native):
 
 def test_default_options(native):
     o = native.cc_default_options()
-    assert o.max_sweeps == 20 and o.debug_checks == 0 and o.table_log2 == 0
-    assert list(o.reserved) == [0] * 5
+    assert o.max_sweeps == 20 and o.debug_checks == 0 and o.table_log2 == 0 and o.table_start_log2 == 0
+    assert list(o.reserved) == [0] * 4
 
 
 def _create_status(native, n, nnz, row_off, col, k, labels, opt=None):

@@ -278,6 +278,73 @@ def test_run_timing_and_launch_count(cc):
         sweep_ms, prop_ms = job.last_run_timing()
         assert len(sweep_ms) == len(prop_ms) == done
         assert np.all(sweep_ms > 0) and np.all(prop_ms > 0) and np.all(prop_ms <= sweep_ms)
-        assert job.launch_count() - base == 1 + 20 * 13
+        assert job.launch_count() - base == 1 + 20 * 18
         job.sweep()
         assert len(job.last_run_timing()[0]) == 1
+
+
+def _hub_case(n_nbr, clusters_of, pair_with_leaf, seed):
+    """Vertex 0 joined to vertices 1..n_nbr; the warm-start consensus puts the
+    neighbours in the clusters given by clusters_of (optionally each with a
+    private leaf), and vertex 0 in a two-member cluster with the last vertex."""
+    rng = np.random.default_rng(seed)
+    leaves = n_nbr if pair_with_leaf else 0
+    n = 1 + n_nbr + leaves + 1
+    pairs = [(0, i) for i in range(1, n_nbr + 1)]
+    if pair_with_leaf:
+        pairs += [(i, n_nbr + i) for i in range(1, n_nbr + 1)]
+    pairs += [(0, n - 1)]
+    ro, col = _edges(n, pairs)
+    C = np.arange(n, dtype=np.int32)
+    for i in range(1, n_nbr + 1):
+        C[i] = clusters_of(i)
+        if pair_with_leaf:
+            C[n_nbr + i] = C[i]
+    C[n - 1] = 0
+    lab = rng.integers(0, 3, (7, n)).astype(np.int32)
+    return ro, col, lab, C
+
+
+@pytest.mark.parametrize("case", ["own_plus_32_tables", "repeats_across_chunks", "seen_set_full"])
+def test_warm_start_hubs(cc, case):
+    """Proposal edge cases: 33 table-scored clusters in one chunk (own cluster
+    plus 32 neighbours' two-member clusters), candidates repeated across
+    32-wide chunks, and more distinct candidates than the seen-set holds."""
+    if case == "own_plus_32_tables":
+        ro, col, lab, C = _hub_case(40, lambda i: i, True, 1)
+    elif case == "repeats_across_chunks":
+        ro, col, lab, C = _hub_case(100, lambda i: 1 + (i - 1) % 5, False, 2)
+    else:
+        ro, col, lab, C = _hub_case(200, lambda i: i, True, 3)
+    F = oracle.objective(lab, C)
+    with cc.Consensus(ro, col, lab) as job:
+        job.set_cluster_ids(C)
+        Cs, Fs = C, F
+        for _ in range(8):
+            r = oracle.sync_step(ro, col, lab, Cs, Fs)
+            assert job.sweep() == r.stats
+            np.testing.assert_array_equal(job.cluster_ids(), r.C)
+            if r.stats["proposals"] == 0:
+                break
+            Cs, Fs = r.C, r.stats["F"]
+
+
+def test_table_retry_path(cc):
+    """A starting capacity too small for the first sweep's new keys: the sweep
+    is abandoned before it commits, retried in twice the capacity, and the run
+    equals the oracle's (including through later shrinks and rebuilds)."""
+    c = make_config("lfr", n=28000, k=8, cmin=20, cmax=1000, max_deg=500, seed=11)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    ref = oracle.sync_run(ro, col, lab, 20)
+    o = cc.cc_default_options()
+    # 262,144 slots for 224,000 keys at the start: the first sweep's ~16,000
+    # new keys cross the 7/8 fill limit
+    o.table_start_log2 = 18
+    with cc.Consensus(ro, col, lab, o) as job:
+        assert job.run_until_converged(20) == ref.sweeps
+        assert job.history() == ref.stats
+        np.testing.assert_array_equal(job.cluster_ids(), ref.C)
+        ts = job.table_stats()
+        assert ts["retries"] >= 1 and ts["rebuilds"] >= 2
+        assert ts["live_keys"] <= ts["used_slots"] <= ts["capacity"] <= ts["max_capacity"]
+        assert job.objective_recompute() == ref.F
