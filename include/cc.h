@@ -198,11 +198,42 @@ cc_status cc_cluster_ids_dev(cc_ctx* ctx, const int32_t** out);
 
 /* Message of the last failure on this context ("" if none).  Owned by the
  * context; valid until the next call on it.  A NULL ctx gives the message of
- * the last failed creation in this thread. */
+ * the last failed creation or context-free call in this thread. */
 const char* cc_last_error(const cc_ctx* ctx);
 
 /* Frees every resource of the context.  NULL is allowed. */
 void cc_destroy(cc_ctx* ctx);
+
+/* ---- allocation-free output renumbering --------------------------------
+ * The paper has no counterpart to this call; it serves callers of the
+ * library.  It does what cc_consensus_labels does to a context's clusters,
+ * but on caller-owned device buffers and without allocating any device
+ * memory: no cudaMalloc, cudaFree or allocating library routine is called.
+ * It is for code that cannot allocate at that point, e.g. code running under
+ * a framework whose memory pool already holds the GPU's memory, or a
+ * latency-bound path that must not pay for cudaMalloc / cudaFree (which can
+ * synchronise the device).  Its temporary arrays live in one fixed array
+ * compiled into the library: every GPU that loads libcc.so holds
+ * CC_NOALLOC_SCRATCH_INTS ints (about 17 MB) of it until the process exits.
+ *
+ *   n           number of entries, 1 <= n <= CC_NOALLOC_MAX_N (else CC_ERR_INVALID)
+ *   ids_dev     int32[n] device: cluster ids, each in [0, n) (else CC_ERR_INVALID),
+ *               e.g. the array given by cc_cluster_ids_dev
+ *   labels_dev  int32[n] device, written: ids renumbered 0..b-1 in order of
+ *               first appearance by index
+ *   stream      cudaStream_t to run on (NULL: the legacy default stream); the
+ *               call synchronises it before returning
+ *
+ * The first call on each device looks up the device address of the fixed
+ * array (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the array, so calls
+ * that overlap on the GPU (other streams, other host threads) race and give
+ * wrong labels: serialise them.  Each call resets the part it needs, so
+ * nothing carries over from the previous call.  Errors are reported through
+ * cc_last_error(NULL). */
+#define CC_NOALLOC_MAX_N (1 << 21)
+#define CC_NOALLOC_SCRATCH_INTS (2 * CC_NOALLOC_MAX_N + CC_NOALLOC_MAX_N / 1024 + 64)
+cc_status cc_renumber_noalloc(int32_t n, const int32_t* ids_dev, int32_t* labels_dev, void* stream);
 
 #ifdef __cplusplus
 }

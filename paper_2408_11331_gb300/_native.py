@@ -22,7 +22,11 @@ STATUS_NAMES = {0: "CC_OK", 1: "CC_ERR_INVALID", 2: "CC_ERR_OOM", 3: "CC_ERR_CUD
 # Every symbol include/cc.h declares; the CPU test suite checks the library exports them.
 EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", "cc_reset", "cc_set_cluster_ids", "cc_sweep",
            "cc_run_until_converged", "cc_last_run_timing", "cc_table_stats", "cc_launch_count", "cc_history", "cc_objective", "cc_objective_recompute",
-           "cc_consensus_labels", "cc_cluster_ids", "cc_cluster_ids_dev", "cc_last_error", "cc_destroy")
+           "cc_consensus_labels", "cc_cluster_ids", "cc_cluster_ids_dev", "cc_last_error", "cc_destroy",
+           "cc_renumber_noalloc")
+
+# Largest n accepted by cc_renumber_noalloc (its built-in scratch holds 2 n ints).
+CC_NOALLOC_MAX_N = 1 << 21
 
 
 class CCError(RuntimeError):
@@ -99,6 +103,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cc_last_error.argtypes = [P]
     lib.cc_destroy.restype = None
     lib.cc_destroy.argtypes = [P]
+    lib.cc_renumber_noalloc.restype = c.c_int
+    lib.cc_renumber_noalloc.argtypes = [c.c_int32, P, P, P]
     return lib
 
 
@@ -241,3 +247,9 @@ def cc_last_error(ctx=None) -> str:
 
 def cc_destroy(ctx):
     lib.cc_destroy(ctx)
+
+
+def cc_renumber_noalloc(n: int, ids_ptr: int, labels_ptr: int, stream: int = 0):
+    """Renumbers n device ids (ids_ptr) into labels_ptr without allocating device memory."""
+    _check(lib.cc_renumber_noalloc(n, ctypes.c_void_p(ids_ptr), ctypes.c_void_p(labels_ptr),
+                                   ctypes.c_void_p(stream or None)), None)

@@ -711,3 +711,12 @@ void cc_destroy(cc_ctx* c)
 }
 
 }  // extern "C"
+
+namespace ccg {
+
+void set_thread_error(const std::string& msg)
+{
+    g_create_error = msg;
+}
+
+}  // namespace ccg

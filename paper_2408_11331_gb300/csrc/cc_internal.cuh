@@ -17,6 +17,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "cc.h"
@@ -172,6 +173,10 @@ cudaError_t launch_state_from_ids(const SweepArgs& a, cudaStream_t s);
 // conditional: only if st->rebuild is set (decided on the device).
 cudaError_t launch_table_rebuild(const SweepArgs& a, bool conditional, cudaStream_t s);
 cudaError_t launch_objective_recompute(const SweepArgs& a, cudaStream_t s);
+
+// ---- api.cu ----
+// Message reported by cc_last_error(NULL) in this thread.
+void set_thread_error(const std::string& msg);
 
 // ---- launch wrappers (sweep.cu) ----
 cudaError_t launch_run_begin(DevState* st, int limit, cudaStream_t s);
