@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--max-sweeps", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sweep-mode", type=int, default=0, choices=[0, 1, 2],
+                   help="0 automatic, 1 staged deltas, 2 rebuild (identical results)")
     return p.parse_args()
 
 
@@ -222,7 +224,9 @@ def main():
     nnz = len(col)
     stream = torch.cuda.Stream()
 
-    job = ccg.Consensus(ro, col, lab)
+    opts = ccg.cc_default_options()
+    opts.sweep_mode = args.sweep_mode
+    job = ccg.Consensus(ro, col, lab, opts)
     job.set_stream(stream.cuda_stream)
     for _ in range(max(args.warmup, 3)):
         job.reset()
@@ -295,7 +299,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        j2 = ccg.Consensus(ro_h, col_h, lab_h)
+        j2 = ccg.Consensus(ro_h, col_h, lab_h, opts)
         e2e_sweeps += j2.run_until_converged(args.max_sweeps)
         ccg._native.cc_consensus_labels(j2._ctx, n, out_h)
         j2.close()

@@ -64,7 +64,13 @@ typedef struct {
                                automatic (>= 2 k n).  The capacity in use then follows the
                                live keys; a sweep that would fill it is abandoned before
                                it commits anything and retried in twice the capacity */
-    int32_t reserved[4];    /* must be zero */
+    int32_t sweep_mode;     /* how a sweep evaluates dF of its kept moves P1 (the results are
+                               identical): 0 = automatic (a rebuild of the contingency hash
+                               from the tentatively moved consensus when more than n/8
+                               vertices propose, otherwise staged count deltas); 1 = always
+                               staged deltas (the hash is built at the singleton start);
+                               2 = always a rebuild */
+    int32_t reserved[3];    /* must be zero */
 } cc_options;
 
 /* State of the contingency hash of a context. */
@@ -153,17 +159,19 @@ cc_status cc_sweep(cc_ctx* ctx, cc_sweep_info* info);
 
 /* Runs sweeps until one has no proposal (the stopping condition of The
  * algorithm) or max_sweeps sweeps ran (max_sweeps <= 0: the option's limit).
- * The whole loop is one CUDA-graph submission (max_sweeps sweeps unrolled, each
- * skipped on the device once the run has stopped) and one synchronisation.
+ * Sweeps are submitted as CUDA graphs of up to 4 unrolled sweeps (a sweep is
+ * skipped on the device once the run has stopped); the host reads the stop
+ * flag after each graph, so a run costs one synchronisation per 4 sweeps.
  * *sweeps_done (may be NULL) counts every sweep run, the final empty one
  * included.  Errors as cc_sweep. */
 cc_status cc_run_until_converged(cc_ctx* ctx, int32_t max_sweeps, int32_t* sweeps_done);
 
 /* Device time of each sweep of the last cc_run_until_converged / cc_sweep
- * call, from CUDA events recorded inside its graph on the context's stream:
+ * call, from CUDA events recorded inside its graphs on the context's stream:
  * sweep_ms[s] covers sweep s (all its kernels), propose_ms[s] its proposal
- * kernel.  At most max entries are written to each non-NULL array; *count
- * receives the number of sweeps that ran. */
+ * kernels (k_own, k_edges, k_collect).  At most max entries are written to
+ * each non-NULL array; *count receives the number of sweeps timed.  A sweep
+ * abandoned for lack of table space and retried is timed once per attempt. */
 cc_status cc_last_run_timing(cc_ctx* ctx, int32_t max, float* sweep_ms, float* propose_ms, int32_t* count);
 
 /* Current state of the contingency hash (synchronises the stream). */

@@ -38,7 +38,7 @@ class CCError(RuntimeError):
 class cc_options(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("table_log2", ctypes.c_int32), ("table_start_log2", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("sweep_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class cc_table_info(ctypes.Structure):

@@ -19,18 +19,20 @@ struct RunGraph {
 };
 
 struct cc_ctx {
-    int n = 0, k = 0, kp = 0;
+    int n = 0, k = 0, kp = 0, lshift = 0;
     long long nnz = 0;
     int device = 0, sms = 0;
     cudaStream_t stream = nullptr;      // stream used by calls
     cudaStream_t own_stream = nullptr;  // stream created by the context (also used for capture)
     long long* off = nullptr;
     int* col = nullptr;
+    int* src = nullptr;                 // source vertex of each CSR entry
     int* G = nullptr;
     int* C = nullptr;
     int* size = nullptr;
     int* dsize = nullptr;
     unsigned long long* best = nullptr;
+    int* aown = nullptr;                // A_a per vertex (proposal step)
     Slot* table = nullptr;
     int* pv = nullptr;
     int* pa = nullptr;
@@ -40,6 +42,7 @@ struct cc_ctx {
     unsigned int* pslot = nullptr;
     int* scratch = nullptr;             // 3n + n/1024 + 64 ints for the output renumbering
     int* members = nullptr;             // rebuild scratch (n)
+    int4* summ = nullptr;               // per-cluster label summaries (n x kp)
     int* cursor = nullptr;              // rebuild scratch (n)
     int* bsum = nullptr;                // rebuild scratch (n/1024 + 2)
     DevState* st = nullptr;
@@ -47,7 +50,8 @@ struct cc_ctx {
     int hist_cap = 1 << 16;
     SweepArgs args{};
     std::map<int, RunGraph> graphs;
-    int last_limit = 0;                 // limit of the last run (for its timing)
+    std::vector<float> sweep_ms;        // device time of each sweep of the last run
+    std::vector<float> propose_ms;      // ... and of its proposal kernels
     long long launches = 0;             // kernels launched so far
     int grid = 0;
     long long partition_sq = 0, F0 = 0;
@@ -137,6 +141,15 @@ cc_status check_device_error(cc_ctx* c, const DevState& s)
 
 cc_status objective_recompute(cc_ctx* c, long long* out)
 {
+    DevState pre;
+    cc_status rp = read_state(c, &pre);
+    if (rp != CC_OK) return rp;
+    if (!pre.tvalid) {
+        // no table yet (singleton start): build it from C first
+        CC_CUDA(c, cudaMemcpyAsync(&c->st->new_mask, &pre.mask, sizeof(pre.mask), cudaMemcpyHostToDevice, c->stream));
+        CC_CUDA(c, launch_table_rebuild(c->args, false, c->stream));
+        c->launches += kKernelsPerRebuild;
+    }
     CC_CUDA(c, launch_objective_recompute(c->args, c->stream));
     c->launches += 1;
     DevState s;
@@ -166,8 +179,16 @@ cc_status start_state(cc_ctx* c)
     s.mask = c->cap_start - 1;
     CC_CUDA(c, cudaMemcpyAsync(c->st, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
     CC_CUDA(c, launch_init_state(c->args, c->stream));
-    CC_CUDA(c, launch_table_rebuild(c->args, false, c->stream));
-    c->launches += 1 + kKernelsPerRebuild;
+    if (c->opt.sweep_mode == 1) {
+        // staged deltas need the singleton counts in the table from the start
+        CC_CUDA(c, launch_table_rebuild(c->args, false, c->stream));
+        c->launches += 1 + kKernelsPerRebuild;
+    } else {
+        // the first sweep rebuilds the table itself (it is always heavy);
+        // the summary rows of singletons follow from the label rows
+        CC_CUDA(c, launch_singleton_summaries(c->args, c->stream));
+        c->launches += 2;
+    }
     DevState r;
     cc_status rc = read_state(c, &r);
     if (rc != CC_OK) return rc;
@@ -216,24 +237,41 @@ cc_status ensure_graph(cc_ctx* c, int limit, RunGraph** out)
     return CC_OK;
 }
 
+// Sweeps per graph launch: a run launches the graph until the device says the
+// run has stopped, so at most kChunk - 1 skipped sweep bodies are submitted
+// after the last sweep (each costs its kernels' launch latency).
+constexpr int kChunk = 4;
+
 cc_status run(cc_ctx* c, int limit, int* done)
 {
+    const int chunk = limit < kChunk ? limit : kChunk;
     RunGraph* g = nullptr;
-    cc_status r = ensure_graph(c, limit, &g);
+    cc_status r = ensure_graph(c, chunk, &g);
     if (r != CC_OK) return r;
     CC_CUDA(c, launch_run_begin(c->st, limit, c->stream));
+    c->launches += 1;
+    c->sweep_ms.clear();
+    c->propose_ms.clear();
     DevState st;
-    // a sweep abandoned for lack of table space is retried in the next graph
-    // body, so a launch can end before the run does; relaunch until it stops
-    for (int launch = 0; launch < 64; ++launch) {
+    int before = 0;
+    // a sweep abandoned for lack of table space is retried in the next body,
+    // so the number of launches is bounded by the limit plus the retries
+    for (int launch = 0; launch < limit + 64; ++launch) {
         CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
-        c->launches += (long long)limit * kKernelsPerSweep;
+        c->launches += (long long)chunk * kKernelsPerSweep;
         r = read_state(c, &st);
         if (r != CC_OK) return r;
+        const int ran = st.run_sweeps - before;
+        for (int b = 0; b < ran && b < chunk; ++b) {
+            float x = 0.f, y = 0.f;
+            CC_CUDA(c, cudaEventElapsedTime(&x, g->bound[b], g->bound[b + 1]));
+            CC_CUDA(c, cudaEventElapsedTime(&y, g->prop[2 * b], g->prop[2 * b + 1]));
+            c->sweep_ms.push_back(x);
+            c->propose_ms.push_back(y);
+        }
+        before = st.run_sweeps;
         if (st.stop || st.err) break;
     }
-    c->launches += 1;
-    c->last_limit = limit;
     r = check_device_error(c, st);
     if (r != CC_OK) return r;
     if (!st.stop) return fail(c, CC_ERR_TABLE_FULL, "sweep retries did not converge");
@@ -265,12 +303,14 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
         if (opt->table_log2 < 0 || opt->table_log2 > 40) return fail(nullptr, CC_ERR_INVALID, "table_log2 out of range");
         if (opt->table_start_log2 < 0 || opt->table_start_log2 > 40)
             return fail(nullptr, CC_ERR_INVALID, "table_start_log2 out of range");
+        if (opt->sweep_mode < 0 || opt->sweep_mode > 2) return fail(nullptr, CC_ERR_INVALID, "sweep_mode must be 0, 1 or 2");
     }
 
     cc_ctx* c = new cc_ctx();
     c->n = n;
     c->k = k;
     c->kp = (k + 3) & ~3;
+    while ((1LL << c->lshift) < n) ++c->lshift;
     c->nnz = nnz;
     if (opt) c->opt = *opt;
     else cc_default_options(&c->opt);
@@ -299,6 +339,8 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
 
     CC_TRY(dalloc(c, &c->off, (size_t)n + 1));
     CC_TRY(dalloc(c, &c->col, (size_t)nnz));
+    CC_TRY(dalloc(c, &c->src, (size_t)nnz));
+    CC_TRY(dalloc(c, &c->aown, (size_t)n));
     CC_TRY(dalloc(c, &c->G, (size_t)n * c->kp));
     CC_TRY(dalloc(c, &c->C, (size_t)n));
     CC_TRY(dalloc(c, &c->size, (size_t)n));
@@ -313,6 +355,7 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
     CC_TRY(dalloc(c, &c->pslot, 2 * (size_t)kn));
     CC_TRY(dalloc(c, &c->scratch, 3 * (size_t)n + (size_t)n / 1024 + 64));
     CC_TRY(dalloc(c, &c->members, (size_t)n));
+    CC_TRY(dalloc(c, &c->summ, (size_t)n * c->kp));
     CC_TRY(dalloc(c, &c->cursor, (size_t)n));
     CC_TRY(dalloc(c, &c->bsum, (size_t)n / 1024 + 2));
     CC_TRY(dalloc(c, &c->st, 1));
@@ -329,6 +372,7 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
     DevState s;
     if (read_state(c, &s) != CC_OK) return bail(CC_ERR_CUDA);
     if (s.err) return bail(fail(c, CC_ERR_INVALID, "malformed CSR: offsets must start at 0, end at nnz and not decrease; columns must lie in [0, n)"));
+    CC_TRY(launch_fill_src(n, c->off, c->src, c->stream));
 
     // label compaction (scratch: the label map and, for host input, a device copy)
     {
@@ -342,7 +386,8 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
         }
         if (e == cudaSuccess) e = cudaMalloc(&lmap, 16 * lcap);
         if (e == cudaSuccess)
-            e = launch_compact_labels(n, k, c->kp, on_device ? labels : dlabels, c->G, lmap, lcap - 1, c->st, c->stream);
+            e = launch_compact_labels(n, k, c->kp, c->lshift, on_device ? labels : dlabels, c->G, lmap, lcap - 1, c->st,
+                                      c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (dlabels) cudaFree(dlabels);
         if (lmap) cudaFree(lmap);
@@ -363,12 +408,17 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
     a.nnz = nnz;
     a.off = c->off;
     a.col = c->col;
+    a.src = c->src;
+    a.aown = c->aown;
     a.G = c->G;
     a.C = c->C;
     a.size = c->size;
     a.dsize = c->dsize;
     a.best = c->best;
     a.table = c->table;
+    a.summ = c->summ;
+    a.lshift = c->lshift;
+    a.sweep_mode = c->opt.sweep_mode;
     a.mask_max = cap - 1;
     a.cap_min = cap < 1024 ? cap : 1024;
     a.pv = c->pv;
@@ -586,18 +636,11 @@ cc_status cc_run_until_converged(cc_ctx* c, int32_t max_sweeps, int32_t* sweeps_
 cc_status cc_last_run_timing(cc_ctx* c, int32_t max, float* sweep_ms, float* propose_ms, int32_t* count)
 {
     if (!c) return fail(nullptr, CC_ERR_INVALID, "ctx is NULL");
-    DevState s;
-    cc_status r = read_state(c, &s);
-    if (r != CC_OK) return r;
-    auto it = c->graphs.find(c->last_limit);
-    const int have = it == c->graphs.end() ? 0 : s.run_sweeps;
+    const int have = (int)c->sweep_ms.size();
     if (count) *count = have;
     for (int i = 0; i < have && i < max; ++i) {
-        float a = 0.f, b = 0.f;
-        CC_CUDA(c, cudaEventElapsedTime(&a, it->second.bound[i], it->second.bound[i + 1]));
-        CC_CUDA(c, cudaEventElapsedTime(&b, it->second.prop[2 * i], it->second.prop[2 * i + 1]));
-        if (sweep_ms) sweep_ms[i] = a;
-        if (propose_ms) propose_ms[i] = b;
+        if (sweep_ms) sweep_ms[i] = c->sweep_ms[i];
+        if (propose_ms) propose_ms[i] = c->propose_ms[i];
     }
     return CC_OK;
 }

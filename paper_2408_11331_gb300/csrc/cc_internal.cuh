@@ -3,9 +3,15 @@
 // Device data layout (one consensus job):
 //   off   int64[n+1]   CSR row offsets            col  int32[nnz]  neighbours
 //   G     int32[n][kp] compacted label ids, vertex-major, kp = k rounded up to 4 so
-//                      that each row is 16-byte aligned; g = i*n + rep where rep is
-//                      the least vertex carrying that label in partition i, so g
-//                      identifies (partition, label) and g < k*n. Padding = -1.
+//                      that each row is 16-byte aligned; g = (i << s) | rep where rep
+//                      is the least vertex carrying that label in partition i and
+//                      2^s >= n, so g identifies (partition, label), i = g >> s and
+//                      g < k 2^s < 2 k n.  Padding = -1.
+//   summ  int4[n][kp]  per (cluster x, partition i): {d, m, m2, 0} with d the label id
+//                      that was most frequent in x at the last table rebuild, m the
+//                      exact current count of d in x (kept by every commit) and m2 an
+//                      upper bound on the count of every other label of partition i
+//                      in x (raised by commits, recomputed at rebuilds).
 //   C     int32[n]     cluster id of each vertex (founding-vertex ids)
 //   size  int32[n]     cluster sizes, indexed by cluster id
 //   table Slot[cap]    the contingency counts n(c, i, l) as an open-addressing
@@ -56,6 +62,9 @@ struct DevState {
     int overflow;                // 1: the table ran short during this sweep (nothing committed)
     int abort;                   // 1: the pending rebuild follows an abandoned sweep
     int retries;                 // sweeps abandoned and retried in a larger table
+    int heavy;                   // 1: this sweep evaluates P1 by a rebuild (see sweep.cu)
+    int rollback;                // 1: the heavy sweep's P1 was rejected and is being undone
+    int tvalid;                  // 1: the table holds the counts of the current C
     int rebuilds;                // table rebuilds since creation
     int skip;                    // 1: this sweep does nothing (the run has stopped)
     int stop;                    // 1: the run has stopped
@@ -72,12 +81,17 @@ struct SweepArgs {
     long long nnz;
     const long long* off;
     const int* col;
+    const int* src;             // source vertex of each CSR entry (nnz)
     const int* G;
     int* C;
     int* size;
     int* dsize;                 // staged size deltas
-    unsigned long long* best;   // matching keys per cluster
+    unsigned long long* best;   // bids: per vertex in the proposal step, per cluster in the matching
+    int* aown;                  // A_a of each vertex for the current sweep
     Slot* table;
+    int4* summ;                  // per-cluster label summaries (see above)
+    int lshift;                  // s: label id g = (i << s) | rep
+    int sweep_mode;              // 0 automatic, 1 always staged deltas, 2 always rebuild
     unsigned long long mask_max; // allocated capacity - 1; the active capacity is st->mask + 1
     unsigned long long cap_min;  // smallest active capacity
     int* pv;                    // proposal list: vertex,
@@ -94,7 +108,8 @@ struct SweepArgs {
     int hist_cap;
 };
 
-// 64-bit finaliser of MurmurHash3 (Austin Appleby, public domain).
+// 64-bit finaliser of MurmurHash3 (Austin Appleby, public domain); used by the
+// setup-time label map.
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 {
     z ^= z >> 33;
@@ -105,9 +120,34 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
     return z;
 }
 
+// Slot hash of a (cluster, label id) key: the two 32-bit halves mixed with odd
+// multipliers, then the 32-bit MurmurHash3 finaliser.  Capacities stay below
+// 2^32 slots (at most 4 k n rounded up, with 3 k n < 2^31).
+__device__ __forceinline__ unsigned long long hash_key(unsigned long long key)
+{
+    unsigned h = ((unsigned)(key >> 32) * 0x9E3779B1u) ^ ((unsigned)key * 0x85EBCA77u);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
 __device__ __forceinline__ unsigned long long ckey(int c, int g)
 {
     return ((unsigned long long)(unsigned)c << 32) | (unsigned)g;
+}
+
+// Keeps the summary row of the slot's (cluster, partition) valid after its
+// count changed by d to newc: the count of the row's label is exact, the
+// bound on the other labels only rises.
+__device__ __forceinline__ void summ_update(int4* summ, int kp, int lshift, unsigned long long key, int d, int newc)
+{
+    const int x = (int)(key >> 32), g = (int)(unsigned)(key & 0xffffffffull);
+    int4* S = summ + (long long)x * kp + (g >> lshift);
+    if (S->x == g) atomicAdd(&S->y, d);
+    else if (d > 0) atomicMax(&S->z, newc);
 }
 
 __device__ __forceinline__ void set_err(DevState* st, int code)
@@ -119,7 +159,7 @@ __device__ __forceinline__ void set_err(DevState* st, int code)
 // does not modify the table, so the non-coherent path is allowed.
 __device__ __forceinline__ int table_count_ro(const Slot* t, unsigned long long mask, unsigned long long key)
 {
-    unsigned long long h = mix64(key) & mask;
+    unsigned long long h = hash_key(key) & mask;
     for (unsigned long long p = 0; p <= mask; ++p) {
         ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(t + h));
         if (e.x == key) return (int)(unsigned)(e.y & 0xffffffffull);
@@ -132,7 +172,7 @@ __device__ __forceinline__ int table_count_ro(const Slot* t, unsigned long long 
 // Slot holding key, or -1 (coherent loads; the key must not be inserted concurrently).
 __device__ __forceinline__ long long table_find(const Slot* t, unsigned long long mask, unsigned long long key)
 {
-    unsigned long long h = mix64(key) & mask;
+    unsigned long long h = hash_key(key) & mask;
     for (unsigned long long p = 0; p <= mask; ++p) {
         unsigned long long k = *reinterpret_cast<const volatile unsigned long long*>(&t[h].key);
         if (k == key) return (long long)h;
@@ -148,7 +188,7 @@ __device__ __forceinline__ long long table_find_or_insert(Slot* t, unsigned long
                                                           unsigned long long key, bool* inserted)
 {
     *inserted = false;
-    unsigned long long h = mix64(key) & mask;
+    unsigned long long h = hash_key(key) & mask;
     for (unsigned long long p = 0; p <= mask; ++p) {
         unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&t[h].key);
         if (k == key) return (long long)h;
@@ -165,9 +205,12 @@ __device__ __forceinline__ long long table_find_or_insert(Slot* t, unsigned long
 // ---- launch wrappers (setup.cu) ----
 cudaError_t launch_validate(int n, long long nnz, const long long* off, const int* col, DevState* st,
                             cudaStream_t s);
-cudaError_t launch_compact_labels(int n, int k, int kp, const int* labels, int* G, void* lmap,
+cudaError_t launch_fill_src(int n, const long long* off, int* src, cudaStream_t s);
+cudaError_t launch_compact_labels(int n, int k, int kp, int lshift, const int* labels, int* G, void* lmap,
                                   unsigned long long lmask, DevState* st, cudaStream_t s);
 cudaError_t launch_init_state(const SweepArgs& a, cudaStream_t s);
+// Summary rows of the singleton start ({g_i(v), 1, 0} for cluster v).
+cudaError_t launch_singleton_summaries(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_state_from_ids(const SweepArgs& a, cudaStream_t s);
 // Rebuild of the table from C into st->new_mask + 1 slots, then st->mask = st->new_mask.
 // conditional: only if st->rebuild is set (decided on the device).
@@ -181,10 +224,9 @@ void set_thread_error(const std::string& msg);
 // ---- launch wrappers (sweep.cu) ----
 cudaError_t launch_run_begin(DevState* st, int limit, cudaStream_t s);
 // One sweep (13 kernels); prop0/prop1 (may be null) are recorded around the proposal kernel.
-constexpr int kKernelsPerRebuild = 8;
-constexpr int kKernelsPerSweep = 10 + kKernelsPerRebuild;
+constexpr int kKernelsPerRebuild = 11;
+constexpr int kKernelsPerSweep = 18 + 3 * kKernelsPerRebuild;
 cudaError_t launch_sweep(const SweepArgs& a, int grid, cudaStream_t s, cudaEvent_t prop0, cudaEvent_t prop1);
-size_t propose_smem_bytes(int kp);
 cudaError_t prepare_propose(int kp, int* blocks_per_sm);
 
 }  // namespace ccg

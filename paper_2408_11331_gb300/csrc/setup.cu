@@ -65,6 +65,13 @@ __global__ void k_validate(int n, long long nnz, const long long* __restrict__ o
     }
 }
 
+__global__ void k_fill_src(int n, const long long* __restrict__ off, int* src)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        for (long long e = off[v]; e < off[v + 1]; ++e) src[e] = (int)v;
+}
+
 __global__ void k_lmap_clear(LSlot* m, unsigned long long cap)
 {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -107,10 +114,10 @@ __global__ void k_label_insert(int n, int k, const int* __restrict__ labels, LSl
     }
 }
 
-// G[v][i] = i*n + rep(i, label).  Tiles of 32 vertices x up to 32 partitions are
+// G[v][i] = (i << lshift) | rep(i, label).  Tiles of 32 vertices x up to 32 partitions are
 // transposed through shared memory so both the label reads and the row writes
 // are coalesced.
-__global__ void k_label_assign(int n, int k, int kp, const int* __restrict__ labels, const LSlot* m,
+__global__ void k_label_assign(int n, int k, int kp, int lshift, const int* __restrict__ labels, const LSlot* m,
                                unsigned long long mask, int* __restrict__ G, DevState* st)
 {
     __shared__ int tile[32][33];
@@ -127,7 +134,7 @@ __global__ void k_label_assign(int n, int k, int kp, const int* __restrict__ lab
                 const unsigned long long key = ((unsigned long long)(unsigned)i << 32) | (unsigned)labels[(long long)i * n + v];
                 long long s = lmap_slot(const_cast<LSlot*>(m), mask, key, false);
                 if (s < 0) set_err(st, CC_ERR_INVALID);
-                else g = (int)((long long)i * n + m[s].rep);
+                else g = (i << lshift) | m[s].rep;
             }
             tile[r][tx] = g;
         }
@@ -330,6 +337,51 @@ __global__ void k_table_build(SweepArgs a, int conditional)
     }
 }
 
+// Summary rows of the rebuilt table.  The first 8 bytes of a row are read as
+// one unsigned 64-bit value (count << 32 | label id), so an atomic maximum
+// over the slots of a (cluster, partition) leaves the most frequent label and
+// its count (ties to the larger id); a second pass takes the largest count of
+// the other labels.
+__global__ void k_summ_clear(int4* summ, long long rows, const DevState* st, int conditional)
+{
+    if (rebuild_off(st, conditional)) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride)
+        summ[r] = make_int4(0, 0, 0, 0);
+}
+
+__global__ void k_summ_top(SweepArgs a, int conditional)
+{
+    const DevState* st = a.st;
+    if (rebuild_off(st, conditional)) return;
+    const unsigned long long cap = st->new_mask + 1;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += stride) {
+        const ulonglong2 e = reinterpret_cast<const ulonglong2*>(a.table)[s];
+        const int cnt = (int)(unsigned)(e.y & 0xffffffffull);
+        if (e.x == kEmpty || cnt <= 0) continue;
+        const int x = (int)(e.x >> 32), g = (int)(unsigned)(e.x & 0xffffffffull);
+        const long long row = (long long)x * a.kp + (g >> a.lshift);
+        atomicMax(reinterpret_cast<unsigned long long*>(a.summ + row), ((unsigned long long)(unsigned)cnt << 32) | (unsigned)g);
+    }
+}
+
+__global__ void k_summ_second(SweepArgs a, int conditional)
+{
+    const DevState* st = a.st;
+    if (rebuild_off(st, conditional)) return;
+    const unsigned long long cap = st->new_mask + 1;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += stride) {
+        const ulonglong2 e = reinterpret_cast<const ulonglong2*>(a.table)[s];
+        const int cnt = (int)(unsigned)(e.y & 0xffffffffull);
+        if (e.x == kEmpty || cnt <= 0) continue;
+        const int x = (int)(e.x >> 32), g = (int)(unsigned)(e.x & 0xffffffffull);
+        int4* S = a.summ + (long long)x * a.kp + (g >> a.lshift);
+        if (S->x != g) atomicMax(&S->z, cnt);
+    }
+}
+
 __global__ void k_table_done(DevState* st, int conditional)
 {
     if (rebuild_off(st, conditional)) return;
@@ -338,6 +390,7 @@ __global__ void k_table_done(DevState* st, int conditional)
     st->rebuild = 0;
     st->abort = 0;
     st->rebuilds += 1;
+    st->tvalid = 1;
 }
 
 __global__ void k_objective_recompute(SweepArgs a)
@@ -367,8 +420,14 @@ cudaError_t launch_validate(int n, long long nnz, const long long* off, const in
     return cudaGetLastError();
 }
 
+cudaError_t launch_fill_src(int n, const long long* off, int* src, cudaStream_t s)
+{
+    k_fill_src<<<grid_for(n), kSetupBlock, 0, s>>>(n, off, src);
+    return cudaGetLastError();
+}
+
 // lmap: 16-byte slots, lmask + 1 of them (caller-owned scratch, >= 2 k n).
-cudaError_t launch_compact_labels(int n, int k, int kp, const int* labels, int* G, void* lmap,
+cudaError_t launch_compact_labels(int n, int k, int kp, int lshift, const int* labels, int* G, void* lmap,
                                   unsigned long long lmask, DevState* st, cudaStream_t s)
 {
     LSlot* m = static_cast<LSlot*>(lmap);
@@ -376,8 +435,24 @@ cudaError_t launch_compact_labels(int n, int k, int kp, const int* labels, int* 
     k_lmap_clear<<<grid_for((long long)cap), kSetupBlock, 0, s>>>(m, cap);
     k_label_insert<<<grid_for((long long)n * k), kSetupBlock, 0, s>>>(n, k, labels, m, lmask, st);
     const long long tiles = ((long long)n + 31) / 32 * (((long long)kp + 31) / 32);
-    k_label_assign<<<(int)(tiles < 152 * 16 ? tiles : 152 * 16), 256, 0, s>>>(n, k, kp, labels, m, lmask, G, st);
+    k_label_assign<<<(int)(tiles < 152 * 16 ? tiles : 152 * 16), 256, 0, s>>>(n, k, kp, lshift, labels, m, lmask, G, st);
     k_label_sumsq<<<grid_for((long long)cap), kSetupBlock, 0, s>>>(m, cap, st);
+    return cudaGetLastError();
+}
+
+__global__ void k_summ_singletons(SweepArgs a)
+{
+    const long long rows = (long long)a.n * a.kp;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+        const int i = (int)(r % a.kp);
+        a.summ[r] = i < a.k ? make_int4(a.G[r], 1, 0, 0) : make_int4(-1, 0, 0, 0);
+    }
+}
+
+cudaError_t launch_singleton_summaries(const SweepArgs& a, cudaStream_t s)
+{
+    k_summ_singletons<<<grid_for((long long)a.n * a.kp), kSetupBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -405,6 +480,9 @@ cudaError_t launch_table_rebuild(const SweepArgs& a, bool conditional, cudaStrea
     k_scan_write<<<nb, 1024, 0, s>>>(a.size, a.n, a.bsum, a.cursor, a.st, c);
     k_members_scatter<<<grid_for(a.n), kSetupBlock, 0, s>>>(a.n, a.C, a.cursor, a.members, a.st, c);
     k_table_build<<<grid_for(a.n), kSetupBlock, 0, s>>>(a, c);
+    k_summ_clear<<<grid_for((long long)a.n * a.kp), kSetupBlock, 0, s>>>(a.summ, (long long)a.n * a.kp, a.st, c);
+    k_summ_top<<<grid_for((long long)a.mask_max + 1), kSetupBlock, 0, s>>>(a, c);
+    k_summ_second<<<grid_for((long long)a.mask_max + 1), kSetupBlock, 0, s>>>(a, c);
     k_table_done<<<1, 1, 0, s>>>(a.st, c);
     return cudaGetLastError();
 }

@@ -2,8 +2,10 @@
 // sequence of kernels on one stream so that it can be captured in a CUDA graph:
 //
 //   begin       per-sweep counters; the sweep is skipped once the run has stopped
-//   propose     best move of every vertex against the sweep-start state
-//               (Eq. objective4 with the gain of Eq. objective3)
+//   own/edges/  best move of every vertex against the sweep-start state
+//   collect     (Eq. objective4 with the gain of Eq. objective3): A_a per
+//               vertex, then one lane group per CSR entry bidding its move,
+//               then the proposal list
 //   stage       singleton guard; stage the size and count deltas of the kept
 //               proposals P1 in the table (inserting target keys)
 //   eval        exact dF of applying P1 at once, from the staged deltas
@@ -37,15 +39,6 @@ __device__ __forceinline__ unsigned long long pack_key(int dD, int id)
 __device__ __forceinline__ int key_gain(unsigned long long key)
 {
     return (int)((unsigned)(key >> 32) ^ 0x80000000u);
-}
-
-__device__ __forceinline__ unsigned long long warp_min64(unsigned long long x)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long y = __shfl_xor_sync(kFull, x, o);
-        x = y < x ? y : x;
-    }
-    return x;
 }
 
 __device__ __forceinline__ long long warp_sum64(long long x)
@@ -102,202 +95,360 @@ __global__ void k_begin(DevState* st)
     st->mode = 0;
 }
 
-// Per-warp scratch of the proposal kernel (shared memory).
-struct WarpScratch {
-    int cx[33];    // entries to score: the own cluster (entry 0, when not a singleton), then
-    int cu[33];    // the distinct candidate clusters of the chunk, a neighbour carrying each
-    int cs[33];    // (the only member for a singleton), and their sizes
-    int seen[128]; // candidates already scored for this vertex (degree > 32 only)
-};
+constexpr int kInflight = 4;  // loads per lane issued before the first is used
 
-constexpr int kInflight = 4;  // table probes per lane issued before the first is resolved
-
-// Agreement A_x = sum_i n(x, g_i(v)) of the entry held by this lane's group:
-// the warp is split into groups of gs lanes (gs = 32 / next_pow2(entries)), one
-// entry per group; the lanes of a group share the partitions.  A singleton {u}
-// is scored from u's label row against v's (int4 loads), any other cluster by
-// hash probes with kInflight first loads in flight per lane.  The group's
-// lanes are summed with xor shuffles (groups are aligned, so they stay apart).
-__device__ __forceinline__ int score_entry(const SweepArgs& a, const Slot* __restrict__ table,
-                                           unsigned long long mask, const int* sg, int x, int u, int sx,
-                                           bool valid, int l, int gs)
+__device__ __forceinline__ int group_sum(int x, int gs)
 {
-    int acc = 0;
-    if (valid) {
-        if (sx == 1) {
-            const int4* g4 = reinterpret_cast<const int4*>(a.G + (long long)u * a.kp);
-            const int4* s4 = reinterpret_cast<const int4*>(sg);
-            const int kq = a.kp >> 2;
-            for (int q0 = l; q0 < kq; q0 += gs * 8) {
-                int4 r[8];
+    for (int o = gs >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+// Summary part of A_x(v) for a non-singleton cluster x, lanes of a group over
+// the partitions i = l, l + gs, ...: ex = sum of m where v carries the row's
+// label d (exact there), ub = ex + sum of m2 elsewhere (an upper bound on
+// A_x), nq = number of partitions where v does not carry d.
+__device__ __forceinline__ void summary_part(const SweepArgs& a, const int* __restrict__ gv, int x, int l, int gs,
+                                             int& ex, int& ub, int& nq)
+{
+    ex = 0;
+    ub = 0;
+    nq = 0;
+    const int4* S = a.summ + (long long)x * a.kp;
+    for (int i0 = l; i0 < a.k; i0 += gs * kInflight) {
+        int4 r[kInflight];
+        int g[kInflight];
 #pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const int q = q0 + b * gs;
-                    r[b] = q < kq ? __ldg(g4 + q) : make_int4(-1, -1, -1, -1);
-                }
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const int q = q0 + b * gs;
-                    if (q < kq) {
-                        const int4 s = s4[q];
-                        acc += (r[b].x == s.x) + (r[b].y == s.y) + (r[b].z == s.z) + (r[b].w == s.w);
-                    }
-                }
+        for (int b = 0; b < kInflight; ++b) {
+            const int i = i0 + b * gs;
+            r[b] = make_int4(-1, 0, 0, 0);
+            g[b] = -2;
+            if (i < a.k) {
+                r[b] = __ldg(S + i);
+                g[b] = __ldg(gv + i);
             }
-        } else {
-            for (int i0 = l; i0 < a.k; i0 += gs * kInflight) {
-                unsigned long long key[kInflight], h[kInflight];
-                ulonglong2 ev[kInflight];
+        }
 #pragma unroll
-                for (int b = 0; b < kInflight; ++b) {
-                    const int i = i0 + b * gs;
-                    key[b] = 0;
-                    h[b] = 0;
-                    ev[b] = make_ulonglong2(kEmpty, 0ull);
-                    if (i < a.k) {
-                        key[b] = ckey(x, sg[i]);
-                        h[b] = mix64(key[b]) & mask;
-                        ev[b] = __ldg(reinterpret_cast<const ulonglong2*>(table + h[b]));
-                    }
-                }
-#pragma unroll
-                for (int b = 0; b < kInflight; ++b)
-                    if (i0 + b * gs < a.k) acc += resolve(table, mask, key[b], h[b], ev[b]);
+        for (int b = 0; b < kInflight; ++b) {
+            if (i0 + b * gs < a.k) {
+                const bool eq = g[b] == r[b].x;
+                ex += eq ? r[b].y : 0;
+                ub += eq ? r[b].y : r[b].z;
+                nq += eq ? 0 : 1;
             }
         }
     }
-    for (int o = gs >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+}
+
+// Exact counts of the partitions the summary leaves open (v does not carry
+// the row's label and another label may be present), by hash probes.
+__device__ __forceinline__ int probe_part(const SweepArgs& a, const Slot* __restrict__ table, unsigned long long mask,
+                                          const int* __restrict__ gv, int x, int l, int gs)
+{
+    const int4* S = a.summ + (long long)x * a.kp;
+    int acc = 0;
+    for (int i0 = l; i0 < a.k; i0 += gs * kInflight) {
+        unsigned long long key[kInflight], h[kInflight];
+        ulonglong2 ev[kInflight];
+        bool on[kInflight];
+#pragma unroll
+        for (int b = 0; b < kInflight; ++b) {
+            const int i = i0 + b * gs;
+            on[b] = false;
+            key[b] = 0;
+            h[b] = 0;
+            ev[b] = make_ulonglong2(kEmpty, 0ull);
+            if (i < a.k) {
+                const int4 r = __ldg(S + i);
+                const int g = __ldg(gv + i);
+                on[b] = g != r.x && r.z > 0;
+                if (on[b]) {
+                    key[b] = ckey(x, g);
+                    h[b] = hash_key(key[b]) & mask;
+                    ev[b] = __ldg(reinterpret_cast<const ulonglong2*>(table + h[b]));
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kInflight; ++b)
+            if (on[b]) acc += resolve(table, mask, key[b], h[b], ev[b]);
+    }
     return acc;
 }
 
-// Warp per vertex.  Each chunk of 32 neighbours: the lane holding a neighbour
-// reads its cluster; equal clusters are merged with __match_any_sync (and,
-// past the first chunk, with a per-warp seen-set) and the distinct candidates
-// are compacted into shared memory, after the vertex's own cluster in the
-// first chunk.  The warp then scores all entries at once, one group of lanes
-// per entry (score_entry), and keeps the least packed (dD, id).  Blocks claim
-// 256-vertex tiles and warps claim single vertices from their tile, which
-// balances skewed degrees; proposals are gathered per tile in shared memory
-// and appended with one global atomic per tile.
-__global__ void __launch_bounds__(kBlock) k_propose(SweepArgs a)
+// Partitions in which u and v carry the same label, plus the padding entries
+// of this lane's quads: the two label rows compared as int4 quads.
+__device__ __forceinline__ int row_part(const SweepArgs& a, int u, int v, int l, int gs)
+{
+    const int4* gu = reinterpret_cast<const int4*>(a.G + (long long)u * a.kp);
+    const int4* gw = reinterpret_cast<const int4*>(a.G + (long long)v * a.kp);
+    const int kq = a.kp >> 2;
+    int acc = 0;
+    for (int q0 = l; q0 < kq; q0 += gs * kInflight) {
+        int4 r[kInflight], s[kInflight];
+#pragma unroll
+        for (int b = 0; b < kInflight; ++b) {
+            const int q = q0 + b * gs;
+            r[b] = make_int4(-1, -1, -1, -1);
+            s[b] = make_int4(-3, -3, -3, -3);
+            if (q < kq) {
+                r[b] = __ldg(gu + q);
+                s[b] = __ldg(gw + q);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kInflight; ++b)
+            acc += (r[b].x == s[b].x) + (r[b].y == s[b].y) + (r[b].z == s[b].z) + (r[b].w == s[b].w);
+    }
+    return acc;  // includes the kp - k padding entries (-1 in every row)
+}
+
+// Lanes per vertex (k_own) or per edge (k_edges): about five partitions per lane.
+__host__ __device__ __forceinline__ int lanes_per_item(int k)
+{
+    int gs = 1;
+    while (gs < 32 && gs * 5 < k) gs <<= 1;
+    return gs;
+}
+
+// A_a for every vertex: k for a singleton, else the summary part of its own
+// cluster plus probes of the open partitions.  One group of lanes per vertex.
+__global__ void __launch_bounds__(kBlock) k_own(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip) return;
     const unsigned long long mask = st->mask;
-    extern __shared__ int4 smem4[];
-    int4* sbuf = smem4;                                            // kTile proposals
-    WarpScratch* wsall = reinterpret_cast<WarpScratch*>(smem4 + kTile);
-    int* sG = reinterpret_cast<int*>(wsall + kWarpsPerBlock);      // own label row per warp
-    __shared__ long long s_tile;
-    __shared__ int s_next, s_cnt;
-    __shared__ unsigned long long s_gbase;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    WarpScratch& ws = wsall[w];
-    int* sg = sG + w * a.kp;
-    const int k = a.k;
-    const Slot* __restrict__ table = a.table;
+    const int gs = lanes_per_item(a.k);
+    const int lane = threadIdx.x & 31, l = lane & (gs - 1);
+    const long long groups = (long long)gridDim.x * blockDim.x / gs;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x - lane) / gs; base < a.n;
+         base += groups) {
+        const long long v = base + lane / gs;
+        const bool valid = v < a.n;
+        const int cv = valid ? __ldg(a.C + v) : 0;
+        const int sa = valid ? __ldg(a.size + cv) : 1;
+        const int* gv = a.G + (valid ? v : 0) * (long long)a.kp;
+        int ex = 0, ub = 0, nq = 0, pb = 0;
+        if (sa > 1) {
+            summary_part(a, gv, cv, l, gs, ex, ub, nq);
+            pb = probe_part(a, a.table, mask, gv, cv, l, gs);
+        }
+        const int A = group_sum(ex + pb, gs);
+        if (valid && l == 0) a.aown[v] = sa > 1 ? A : a.k;
+    }
+}
 
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_tile = (long long)atomicAdd(&st->tile_ctr, (unsigned long long)kTile);
-            s_next = 0;
-            s_cnt = 0;
-        }
-        __syncthreads();
-        const long long tile = s_tile;
-        if (tile >= a.n) break;
-        const int tlen = (int)min((long long)kTile, (long long)a.n - tile);
-        for (;;) {
-            int idx = 0;
-            if (lane == 0) idx = atomicAdd(&s_next, 1);
-            idx = __shfl_sync(kFull, idx, 0);
-            if (idx >= tlen) break;
-            const int v = (int)(tile + idx);
-            const long long beg = __ldg(a.off + v), end = __ldg(a.off + v + 1);
-            if (beg == end) continue;  // isolated: never moves
+// One group of lanes per CSR entry (v, u): scores the move of v to C[u]
+// (skipped for self-loops and u in v's own cluster).  A singleton {u} is
+// scored from the two label rows; another cluster from its summary rows, then
+// (unless the lower bound on dD from the summary is already >= 0) from probes
+// of the open partitions.  A move with dD < 0 bids its packed (dD, C[u]) at
+// best[v] with an atomic minimum; repeated candidates bid the same key.  All
+// group reductions are outside the branches, so every lane of the warp takes
+// part in every shuffle.
+__global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
+{
+    DevState* st = a.st;
+    if (st->skip) return;
+    const unsigned long long mask = st->mask;
+    const int gs = lanes_per_item(a.k);
+    const int lane = threadIdx.x & 31, l = lane & (gs - 1);
+    const int k = a.k, pad = a.kp - a.k;
+    const long long groups = (long long)gridDim.x * blockDim.x / gs;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x - lane) / gs; base < a.nnz;
+         base += groups) {
+        const long long e = base + lane / gs;
+        int v = 0, u = 0, x = -1, sx = 0, sa = 0, Aa = 0;
+        if (e < a.nnz) {
+            v = __ldg(a.src + e);
+            u = __ldg(a.col + e);
             const int cv = __ldg(a.C + v);
-            const int sa = __ldg(a.size + cv);
-            const int* gv = a.G + (long long)v * a.kp;
-            for (int i = lane; i < a.kp; i += 32) sg[i] = i < k ? __ldg(gv + i) : -2;
-            const bool use_seen = end - beg > 32;
-            if (use_seen)
-                for (int q = lane; q < 128; q += 32) ws.seen[q] = -1;
-            __syncwarp();
-            int Aa = k;  // A_a = sum_i n(a, g_i(v)); k for a singleton
-            unsigned long long best = kEmpty;
-            for (long long base = beg; base < end; base += 32) {
-                const long long e = base + lane;
-                int u = -1, x = -1;
-                if (e < end) {
-                    u = __ldg(a.col + e);
-                    if (u != v) {
-                        x = __ldg(a.C + u);
-                        if (x == cv) x = -1;
-                    }
-                }
-                const unsigned m = __match_any_sync(kFull, x);
-                bool lead = x >= 0 && (__ffs(m) - 1) == lane;
-                if (use_seen && lead) {
-                    unsigned h = ((unsigned)x * 2654435761u) >> 25;
-                    for (int t = 0; t < 128; ++t, h = (h + 1) & 127) {
-                        const int old = atomicCAS(&ws.seen[h], -1, x);
-                        if (old == -1) break;
-                        if (old == x) { lead = false; break; }
-                    }
-                }
-                const bool own = base == beg && sa > 1;  // the own cluster is scored with the first chunk
-                const int e0 = own ? 1 : 0;
-                const unsigned lb = __ballot_sync(kFull, lead);
-                const int ne = e0 + __popc(lb);
-                if (lane == 0 && own) {
-                    ws.cx[0] = cv;
-                    ws.cu[0] = v;
-                    ws.cs[0] = sa;
-                }
-                if (lead) {
-                    const int p = e0 + __popc(lb & lt);
-                    ws.cx[p] = x;
-                    ws.cu[p] = u;
-                    ws.cs[p] = __ldg(a.size + x);
-                }
-                __syncwarp();
-                // groups of gs lanes, 32 / gs >= entries (33 entries: two passes of 32)
-                for (int p0 = 0; p0 < ne; p0 += 32) {
-                    const int cnt = min(32, ne - p0);
-                    const int gs = cnt > 16 ? 1 : cnt > 8 ? 2 : cnt > 4 ? 4 : cnt > 2 ? 8 : cnt > 1 ? 16 : 32;
-                    const int j = p0 + lane / gs, l = lane & (gs - 1);
-                    const bool valid = j < ne;
-                    const int xj = valid ? ws.cx[j] : 0, uj = valid ? ws.cu[j] : 0, sj = valid ? ws.cs[j] : 0;
-                    const int A = score_entry(a, table, mask, sg, xj, uj, sj, valid, l, gs);
-                    if (own && p0 == 0) Aa = __shfl_sync(kFull, A, 0);
-                    if (valid && l == 0 && !(own && j == 0)) {
-                        const int dD = 2 * (Aa - k - A) - k * (sa - 1 - sj);
-                        const unsigned long long kk = pack_key(dD, xj);
-                        best = kk < best ? kk : best;
-                    }
-                }
-                __syncwarp();
+            if (u != v) {
+                x = __ldg(a.C + u);
+                if (x == cv) x = -1;
             }
-            best = warp_min64(best);
-            if (lane == 0 && best != kEmpty && key_gain(best) < 0) {
+            if (x >= 0) {
+                sx = __ldg(a.size + x);
+                sa = __ldg(a.size + cv);
+                Aa = __ldg(a.aown + v);
+            }
+        }
+        const bool single = x >= 0 && sx == 1;
+        const bool table = x >= 0 && sx > 1;
+        const int* gv = a.G + (long long)v * a.kp;
+        int rc = 0, ex = 0, ub = 0, nq = 0;
+        if (single) rc = row_part(a, u, v, l, gs);
+        if (table) summary_part(a, gv, x, l, gs, ex, ub, nq);
+        rc = group_sum(rc, gs);
+        ex = group_sum(ex, gs);
+        ub = group_sum(ub, gs);
+        const bool open = table && 2 * (Aa - k - ub) - k * (sa - 1 - sx) < 0;
+        int pb = 0;
+        if (open) pb = probe_part(a, a.table, mask, gv, x, l, gs);
+        pb = group_sum(pb, gs);
+        if ((single || open) && l == 0) {
+            const int A = single ? rc - pad : ex + pb;
+            const int dD = 2 * (Aa - k - A) - k * (sa - 1 - sx);
+            if (dD < 0) atomicMin(&a.best[v], pack_key(dD, x));
+        }
+    }
+}
+
+// Turns the bids into the proposal list (v, a, b, dD) and clears best[].
+// Each block gathers its proposals in shared memory and appends them with one
+// global atomic.
+__global__ void __launch_bounds__(kBlock) k_collect(SweepArgs a)
+{
+    DevState* st = a.st;
+    if (st->skip) return;
+    __shared__ int4 sbuf[kBlock];
+    __shared__ int s_cnt;
+    __shared__ unsigned long long s_base;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < a.n; b0 += stride) {
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        const long long v = b0 + threadIdx.x;
+        if (v < a.n) {
+            const unsigned long long key = a.best[v];
+            if (key != kEmpty) {
+                a.best[v] = kEmpty;
                 const int p = atomicAdd(&s_cnt, 1);
-                sbuf[p] = make_int4(v, cv, (int)(unsigned)(best & 0xffffffffull), key_gain(best));
+                sbuf[p] = make_int4((int)v, a.C[v], (int)(unsigned)(key & 0xffffffffull), key_gain(key));
             }
-            __syncwarp();
         }
         __syncthreads();
-        if (threadIdx.x == 0 && s_cnt > 0) s_gbase = atomicAdd(&st->nprop, (unsigned long long)s_cnt);
+        if (threadIdx.x == 0 && s_cnt > 0) s_base = atomicAdd(&st->nprop, (unsigned long long)s_cnt);
         __syncthreads();
         for (int p = threadIdx.x; p < s_cnt; p += blockDim.x) {
-            const int4 e = sbuf[p];
-            const unsigned long long j = s_gbase + p;
-            a.pv[j] = e.x;
-            a.pa[j] = e.y;
-            a.pb[j] = e.z;
-            a.pg[j] = e.w;
+            const int4 q = sbuf[p];
+            const unsigned long long j = s_base + p;
+            a.pv[j] = q.x;
+            a.pa[j] = q.y;
+            a.pb[j] = q.z;
+            a.pg[j] = q.w;
         }
         __syncthreads();
+    }
+}
+
+// ---- heavy sweeps --------------------------------------------------------
+// When a large share of the vertices proposes (|P| > n / 8, or always with
+// sweep_mode 2, never with sweep_mode 1), or the table
+// does not hold the counts of C yet (the singleton start), dF(P1) is taken
+// from a rebuild instead of from staged deltas: P1 is applied to C in place
+// (the movers' old clusters stay in the proposal list), the table and its
+// summary rows are rebuilt from the new C, and F' - F is dF(P1) exactly.  If
+// it is negative, P1 is committed as it stands (mode 3); otherwise the moves
+// are undone, the table is rebuilt from C again and the matching fallback
+// runs as in a light sweep (mode 2).
+
+__global__ void k_route(SweepArgs a)
+{
+    DevState* st = a.st;
+    st->heavy = 0;
+    st->rollback = 0;
+    if (st->skip || st->err || st->nprop == 0) return;
+    const bool light = a.sweep_mode == 1 || (a.sweep_mode == 0 && st->nprop * 8 <= (unsigned long long)a.n);
+    if (st->tvalid && light) return;
+    st->heavy = 1;
+    st->recompute = 0;
+    // keys after applying P1: every vertex gives at most k, every mover at most k new ones
+    const unsigned long long kn = (unsigned long long)a.k * a.n;
+    unsigned long long bound = (st->tvalid ? (unsigned long long)st->live : kn) + (unsigned long long)a.k * st->nprop;
+    if (bound > kn) bound = kn;
+    unsigned long long c = a.cap_min;
+    while (c < 2 * bound && c < a.mask_max + 1) c <<= 1;
+    st->new_mask = c - 1;
+    st->rebuild = 1;
+}
+
+// Singleton guard on every proposal (sizes of the sweep start); counts |P1|.
+__global__ void k_h_mark(SweepArgs a)
+{
+    DevState* st = a.st;
+    if (st->skip || !st->heavy) return;
+    const long long np = (long long)st->nprop;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+        const long long j = base + threadIdx.x;
+        bool keep = false;
+        if (j < np) {
+            const int ca = a.pa[j], cb = a.pb[j];
+            keep = !(a.size[ca] == 1 && a.size[cb] == 1) || cb < ca;
+            a.pflag[j] = keep ? 1 : 0;
+        }
+        const unsigned mk = __ballot_sync(kFull, keep);
+        if (lane == 0 && mk) atomicAdd(&st->np1, (unsigned long long)__popc(mk));
+    }
+}
+
+// Applies (sign +1) or undoes (sign -1) the kept proposals on C and the sizes.
+__global__ void k_h_apply(SweepArgs a, int undo)
+{
+    DevState* st = a.st;
+    if (st->skip || !st->heavy || (undo && !st->rollback)) return;
+    const long long np = (long long)st->nprop;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
+        if (!a.pflag[j]) continue;
+        const int ca = a.pa[j], cb = a.pb[j];
+        a.C[a.pv[j]] = undo ? ca : cb;
+        atomicAdd(&a.size[ca], undo ? 1 : -1);
+        atomicAdd(&a.size[cb], undo ? -1 : 1);
+    }
+}
+
+// F' = k sum_c s_c^2 - 2 sum_keys n^2 (+ sum_ij |P_ij|^2, added in k_h_decide)
+// from the rebuilt table.
+__global__ void k_h_eval(SweepArgs a)
+{
+    DevState* st = a.st;
+    if (st->skip || !st->heavy || st->err) return;
+    const unsigned long long mask = st->mask;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long work = mask + 1 > (unsigned long long)a.n ? mask + 1 : (unsigned long long)a.n;
+    for (unsigned long long b0 = (unsigned long long)blockIdx.x * blockDim.x; b0 < work; b0 += stride) {
+        const unsigned long long t = b0 + threadIdx.x;
+        long long acc = 0;
+        if (t < (unsigned long long)a.n) {
+            const long long sz = a.size[t];
+            acc += (long long)a.k * sz * sz;
+        }
+        if (t <= mask) {
+            const ulonglong2 e = reinterpret_cast<const ulonglong2*>(a.table)[t];
+            if (e.x != kEmpty) {
+                const long long c = (int)(unsigned)(e.y & 0xffffffffull);
+                acc -= 2 * c * c;
+            }
+        }
+        block_add64(acc, &st->recompute);
+    }
+}
+
+__global__ void k_h_decide(SweepArgs a)
+{
+    DevState* st = a.st;
+    if (st->skip || !st->heavy) return;
+    if (st->err) {
+        st->mode = 0;
+        return;
+    }
+    const long long dF = st->recompute + st->partition_sq - st->F;
+    st->dF_p1 = st->np1 > 0 ? dF : 0;
+    if (st->np1 > 0 && dF < 0) {
+        st->mode = 3;
+        st->dF = dF;
+        st->moves = st->np1;
+    } else {
+        st->mode = 2;
+        st->dF = 0;
+        st->moves = 0;
+        if (st->np1 > 0) {
+            st->rollback = 1;
+            st->rebuild = 1;
+            st->new_mask = st->mask;
+        }
     }
 }
 
@@ -322,7 +473,7 @@ __device__ __forceinline__ void count_inserts(DevState* st, unsigned mi, unsigne
 __global__ void k_stage(SweepArgs a)
 {
     DevState* st = a.st;
-    if (st->skip || st->err) return;
+    if (st->skip || st->err || st->heavy) return;
     const unsigned long long mask = st->mask;
     const long long total = (long long)st->nprop * a.k;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -373,7 +524,7 @@ __global__ void k_stage(SweepArgs a)
 __global__ void k_eval(SweepArgs a)
 {
     DevState* st = a.st;
-    if (st->skip || st->err || st->overflow) return;
+    if (st->skip || st->err || st->overflow || st->heavy) return;
     const long long total = (long long)st->nprop * a.k;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
@@ -400,7 +551,7 @@ __global__ void k_eval(SweepArgs a)
 
 __global__ void k_decide(DevState* st)
 {
-    if (st->skip) return;
+    if (st->skip || st->heavy) return;
     if (st->err || st->overflow) {
         st->mode = 0;
         return;
@@ -425,7 +576,8 @@ __global__ void k_commit(SweepArgs a)
     DevState* st = a.st;
     if (st->skip || st->err) return;
     const int mode = st->mode;
-    if (mode == 0) return;
+    if (mode == 0 || mode == 3) return;
+    const bool staged = !st->heavy;  // only light sweeps staged deltas to undo
     const long long total = (long long)st->nprop * a.k;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
@@ -451,11 +603,12 @@ __global__ void k_commit(SweepArgs a)
                         if (d) {
                             const int old = atomicAdd(&s->cnt, d);
                             live += (old == 0) - (old + d == 0);
+                            summ_update(a.summ, a.kp, a.lshift, s->key, d, old + d);
                         }
                     }
                 }
             } else {
-                if (a.pflag[j]) {
+                if (staged && a.pflag[j]) {
                     a.table[a.pslot[2 * t]].dlt = 0;
                     a.table[a.pslot[2 * t + 1]].dlt = 0;
                     if (i == 0) {
@@ -534,8 +687,11 @@ __global__ void k_match_apply(SweepArgs a)
                 if (sa < 0 || sb < 0) {
                     set_err(st, CC_ERR_INVALID);
                 } else {
-                    if (atomicAdd(&a.table[sa].cnt, -1) == 1) --live;
-                    if (atomicAdd(&a.table[sb].cnt, 1) == 0) ++live;
+                    const int oa = atomicAdd(&a.table[sa].cnt, -1);
+                    const int ob = atomicAdd(&a.table[sb].cnt, 1);
+                    live += (ob == 0) - (oa == 1);
+                    summ_update(a.summ, a.kp, a.lshift, ckey(ca, g), -1, oa - 1);
+                    summ_update(a.summ, a.kp, a.lshift, ckey(cb, g), 1, ob + 1);
                 }
             }
         }
@@ -597,10 +753,10 @@ __global__ void k_end(SweepArgs a)
     // new capacity holds the live keys plus half of k x (moves of this sweep),
     // a forecast of the next sweep's new keys, at load <= 1/2.
     const unsigned long long live = (unsigned long long)st->live;
-    const unsigned long long want = 2 * live + (unsigned long long)a.k * st->moves;
+    const unsigned long long want = 2 * live + (st->heavy ? 0ull : (unsigned long long)a.k * st->moves);
     unsigned long long c = a.cap_min;
     while (c < want && c < a.mask_max + 1) c <<= 1;
-    if (st->used > cap / 2 || (live * 6 < cap && c < cap)) {
+    if (st->tvalid && (st->used > cap / 2 || (live * 6 < cap && c < cap))) {
         st->new_mask = c - 1;
         st->rebuild = 1;
     } else {
@@ -610,17 +766,10 @@ __global__ void k_end(SweepArgs a)
 
 }  // namespace
 
-size_t propose_smem_bytes(int kp)
-{
-    return sizeof(int4) * kTile + sizeof(WarpScratch) * kWarpsPerBlock + sizeof(int) * (size_t)kWarpsPerBlock * kp;
-}
-
 cudaError_t prepare_propose(int kp, int* blocks_per_sm)
 {
-    const size_t smem = propose_smem_bytes(kp);
-    cudaError_t e = cudaFuncSetAttribute(k_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_propose, kBlock, smem);
+    (void)kp;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_edges, kBlock, 0);
 }
 
 cudaError_t launch_run_begin(DevState* st, int limit, cudaStream_t s)
@@ -637,9 +786,25 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, cudaStream_t s, cudaEvent
         cudaError_t e = cudaEventRecordWithFlags(prop0, s, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
-    k_propose<<<grid, kBlock, propose_smem_bytes(a.kp), s>>>(a);
+    k_own<<<grid, kBlock, 0, s>>>(a);
+    k_edges<<<grid, kBlock, 0, s>>>(a);
+    k_collect<<<grid, kBlock, 0, s>>>(a);
     if (prop1) {
         cudaError_t e = cudaEventRecordWithFlags(prop1, s, cudaEventRecordExternal);
+        if (e != cudaSuccess) return e;
+    }
+    k_route<<<1, 1, 0, s>>>(a);
+    k_h_mark<<<g2, kBlock, 0, s>>>(a);
+    k_h_apply<<<g2, kBlock, 0, s>>>(a, 0);
+    {
+        cudaError_t e = launch_table_rebuild(a, true, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_h_eval<<<g2, kBlock, 0, s>>>(a);
+    k_h_decide<<<1, 1, 0, s>>>(a);
+    k_h_apply<<<g2, kBlock, 0, s>>>(a, 1);
+    {
+        cudaError_t e = launch_table_rebuild(a, true, s);
         if (e != cudaSuccess) return e;
     }
     k_stage<<<g2, kBlock, 0, s>>>(a);

@@ -46,21 +46,33 @@ def assert_same(g, ref):
     np.testing.assert_array_equal(g["labels"], oracle.renumber(ref.C))
 
 
-def test_sbm_full_run(cc):
+MODES = [0, 1, 2]  # automatic, always staged deltas, always rebuild
+
+
+def options(cc, **kw):
+    o = cc.cc_default_options()
+    for key, val in kw.items():
+        setattr(o, key, val)
+    return o
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_sbm_full_run(cc, mode):
     c = make_config("sbm")
     ref = oracle.sync_run(c["row_off"], c["col"], c["labels"], 20)
-    assert_same(gpu_run(cc, c["row_off"], c["col"], c["labels"], 20), ref)
+    assert_same(gpu_run(cc, c["row_off"], c["col"], c["labels"], 20, sweep_mode=mode), ref)
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("n,k,seed", [(20000, 8, 11), (5003, 37, 12), (3001, 1, 13), (12000, 64, 14)])
-def test_lfr_stepwise(cc, n, k, seed):
-    """Sweep by sweep: several proposal tiles, ragged tails, k not a multiple of
-    4, k above one warp, and k = 1."""
+def test_lfr_stepwise(cc, n, k, seed, mode):
+    """Sweep by sweep: several lane groups, ragged tails, k not a multiple of
+    4, k above one warp, and k = 1; in every sweep mode."""
     c = make_config("lfr", n=n, k=k, cmin=20, cmax=min(1000, n), max_deg=min(1000, n // 4), seed=seed)
     ro, col, lab = c["row_off"], c["col"], c["labels"]
     C = oracle.singletons(n)
     F = oracle.objective(lab, C)
-    with cc.Consensus(ro, col, lab) as job:
+    with cc.Consensus(ro, col, lab, options(cc, sweep_mode=mode)) as job:
         assert job.objective() == F
         for _ in range(25):
             r = oracle.sync_step(ro, col, lab, C, F)
@@ -73,10 +85,11 @@ def test_lfr_stepwise(cc, n, k, seed):
         assert job.objective_recompute() == F
 
 
-def test_knn_small(cc):
+@pytest.mark.parametrize("mode", MODES)
+def test_knn_small(cc, mode):
     c = make_config("knn", n=6000, comps=30, dim=20, k=12, seed=21)
     ref = oracle.sync_run(c["row_off"], c["col"], c["labels"], 30)
-    assert_same(gpu_run(cc, c["row_off"], c["col"], c["labels"], 30), ref)
+    assert_same(gpu_run(cc, c["row_off"], c["col"], c["labels"], 30, sweep_mode=mode), ref)
 
 
 def _edges(n, pairs):
@@ -128,11 +141,12 @@ def _cases():
 CASES = _cases()
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_edge_cases(cc, name):
+def test_edge_cases(cc, name, mode):
     ro, col, lab = CASES[name]
     ref = oracle.sync_run(ro, col, lab, 60)
-    g = gpu_run(cc, ro, col, lab, 60)
+    g = gpu_run(cc, ro, col, lab, 60, sweep_mode=mode)
     assert_same(g, ref)
     if name == "identical_copies":
         assert g["F"] == 0
@@ -155,7 +169,8 @@ def test_warm_start_swap_fallback(cc):
         np.testing.assert_array_equal(job.cluster_ids(), g["sweep"]["C"])
 
 
-def test_warm_start_fallback_random(cc):
+@pytest.mark.parametrize("mode", MODES)
+def test_warm_start_fallback_random(cc, mode):
     """Starts where each group is split in two halves that want to swap: the
     fallback branch, including partial matchings, against the oracle."""
     seen = 0
@@ -179,7 +194,7 @@ def test_warm_start_fallback_random(cc):
         keep = (group[iu] == group[ju]) & (rng.random(len(iu)) < 0.8) | (rng.random(len(iu)) < 0.05)
         ro, col = csr_from_edges(n, iu[keep], ju[keep])
         F = oracle.objective(lab, C)
-        with cc.Consensus(ro, col, lab) as job:
+        with cc.Consensus(ro, col, lab, options(cc, sweep_mode=mode)) as job:
             job.set_cluster_ids(C)
             assert job.objective() == F
             Cs, Fs = C, F
@@ -219,13 +234,17 @@ def test_errors_leave_state(cc):
 
 
 def test_table_full_is_reported(cc):
-    """A contingency hash far too small: bounded probing reports CC_ERR_TABLE_FULL."""
+    """A contingency hash far too small: bounded probing reports CC_ERR_TABLE_FULL,
+    at creation when the table is built there (staged deltas), else at the
+    first sweep's rebuild."""
     c = make_config("sbm", n=200, communities=4, k=3, seed=8)
-    o = cc.cc_default_options()
-    o.table_log2 = 6
     with pytest.raises(cc.CCError) as e:
-        cc.Consensus(c["row_off"], c["col"], c["labels"], o)
+        cc.Consensus(c["row_off"], c["col"], c["labels"], options(cc, table_log2=6, sweep_mode=1))
     assert e.value.status == 5
+    with cc.Consensus(c["row_off"], c["col"], c["labels"], options(cc, table_log2=6)) as job:
+        with pytest.raises(cc.CCError) as e:
+            job.run_until_converged(20)
+        assert e.value.status == 5
 
 
 def test_reset_and_options(cc):
@@ -278,7 +297,8 @@ def test_run_timing_and_launch_count(cc):
         sweep_ms, prop_ms = job.last_run_timing()
         assert len(sweep_ms) == len(prop_ms) == done
         assert np.all(sweep_ms > 0) and np.all(prop_ms > 0) and np.all(prop_ms <= sweep_ms)
-        assert job.launch_count() - base == 1 + 20 * 18
+        per_sweep = 18 + 3 * 11  # kernels of one unrolled sweep body
+        assert job.launch_count() - base == 1 + ((done + 3) // 4) * 4 * per_sweep
         job.sweep()
         assert len(job.last_run_timing()[0]) == 1
 
@@ -305,8 +325,9 @@ def _hub_case(n_nbr, clusters_of, pair_with_leaf, seed):
     return ro, col, lab, C
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("case", ["own_plus_32_tables", "repeats_across_chunks", "seen_set_full"])
-def test_warm_start_hubs(cc, case):
+def test_warm_start_hubs(cc, case, mode):
     """Proposal edge cases: 33 table-scored clusters in one chunk (own cluster
     plus 32 neighbours' two-member clusters), candidates repeated across
     32-wide chunks, and more distinct candidates than the seen-set holds."""
@@ -317,7 +338,7 @@ def test_warm_start_hubs(cc, case):
     else:
         ro, col, lab, C = _hub_case(200, lambda i: i, True, 3)
     F = oracle.objective(lab, C)
-    with cc.Consensus(ro, col, lab) as job:
+    with cc.Consensus(ro, col, lab, options(cc, sweep_mode=mode)) as job:
         job.set_cluster_ids(C)
         Cs, Fs = C, F
         for _ in range(8):
@@ -337,9 +358,10 @@ def test_table_retry_path(cc):
     ro, col, lab = c["row_off"], c["col"], c["labels"]
     ref = oracle.sync_run(ro, col, lab, 20)
     o = cc.cc_default_options()
-    # 262,144 slots for 224,000 keys at the start: the first sweep's ~16,000
-    # new keys cross the 7/8 fill limit
+    # staged deltas from the start, in 262,144 slots for 224,000 keys: the
+    # first sweep's ~16,000 new keys cross the 7/8 fill limit
     o.table_start_log2 = 18
+    o.sweep_mode = 1
     with cc.Consensus(ro, col, lab, o) as job:
         assert job.run_until_converged(20) == ref.sweeps
         assert job.history() == ref.stats
