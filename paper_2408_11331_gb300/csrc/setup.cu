@@ -350,12 +350,16 @@ __global__ void k_summ_clear(int4* summ, long long rows, const DevState* st, int
         summ[r] = make_int4(0, 0, 0, 0);
 }
 
+// In the first rebuild of a heavy sweep this pass also adds -2 sum n^2 over
+// the new keys to st->recompute (the table part of F').
 __global__ void k_summ_top(SweepArgs a, int conditional)
 {
-    const DevState* st = a.st;
+    DevState* st = a.st;
     if (rebuild_off(st, conditional)) return;
+    const bool eval = st->heavy && !st->rollback;
     const unsigned long long cap = st->new_mask + 1;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    long long sq = 0;
     for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += stride) {
         const ulonglong2 e = reinterpret_cast<const ulonglong2*>(a.table)[s];
         const int cnt = (int)(unsigned)(e.y & 0xffffffffull);
@@ -363,7 +367,9 @@ __global__ void k_summ_top(SweepArgs a, int conditional)
         const int x = (int)(e.x >> 32), g = (int)(unsigned)(e.x & 0xffffffffull);
         const long long row = (long long)x * a.kp + (g >> a.lshift);
         atomicMax(reinterpret_cast<unsigned long long*>(a.summ + row), ((unsigned long long)(unsigned)cnt << 32) | (unsigned)g);
+        sq += (long long)cnt * cnt;
     }
+    if (eval) block_add64(-2 * sq, &st->recompute);
 }
 
 __global__ void k_summ_second(SweepArgs a, int conditional)

@@ -237,59 +237,84 @@ __global__ void __launch_bounds__(kBlock) k_own(SweepArgs a)
     }
 }
 
-// One group of lanes per CSR entry (v, u): scores the move of v to C[u]
-// (skipped for self-loops and u in v's own cluster).  A singleton {u} is
-// scored from the two label rows; another cluster from its summary rows, then
-// (unless the lower bound on dD from the summary is already >= 0) from probes
-// of the open partitions.  A move with dD < 0 bids its packed (dD, C[u]) at
-// best[v] with an atomic minimum; repeated candidates bid the same key.  All
-// group reductions are outside the branches, so every lane of the warp takes
-// part in every shuffle.
+// Foreign CSR entries of one warp, compacted in shared memory.
+struct EdgeScratch {
+    int v[32], u[32], x[32], sx[32], sa[32], Aa[32];
+};
+
+// CSR entries 32 at a time per warp: each lane reads one entry (v, u) and
+// keeps it if u lies in another cluster than v (self-loops and repeats of the
+// same (v, C[u]) inside the warp are dropped); the kept entries are then
+// scored by groups of lanes.  A singleton {u} is scored from the two label
+// rows; another cluster from its summary rows, then (unless the lower bound on
+// dD from the summary is already >= 0) from probes of the open partitions.  A
+// move with dD < 0 bids its packed (dD, C[u]) at best[v] with an atomic
+// minimum.  All group reductions are outside the branches, so every lane of
+// the warp takes part in every shuffle.
 __global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip) return;
+    __shared__ EdgeScratch sh[kWarpsPerBlock];
     const unsigned long long mask = st->mask;
-    const int gs = lanes_per_item(a.k);
-    const int lane = threadIdx.x & 31, l = lane & (gs - 1);
+    const int gs = lanes_per_item(a.k), per = 32 / gs;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, l = lane & (gs - 1);
+    const unsigned lt = (1u << lane) - 1u;
     const int k = a.k, pad = a.kp - a.k;
-    const long long groups = (long long)gridDim.x * blockDim.x / gs;
-    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x - lane) / gs; base < a.nnz;
-         base += groups) {
-        const long long e = base + lane / gs;
-        int v = 0, u = 0, x = -1, sx = 0, sa = 0, Aa = 0;
+    EdgeScratch& es = sh[w];
+    const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
+    for (long long base = ((long long)blockIdx.x * kWarpsPerBlock + w) * 32; base < a.nnz; base += nwarps * 32) {
+        const long long e = base + lane;
+        int v = 0, u = 0, x = -1;
         if (e < a.nnz) {
             v = __ldg(a.src + e);
             u = __ldg(a.col + e);
-            const int cv = __ldg(a.C + v);
             if (u != v) {
                 x = __ldg(a.C + u);
-                if (x == cv) x = -1;
-            }
-            if (x >= 0) {
-                sx = __ldg(a.size + x);
-                sa = __ldg(a.size + cv);
-                Aa = __ldg(a.aown + v);
+                if (x == __ldg(a.C + v)) x = -1;
             }
         }
-        const bool single = x >= 0 && sx == 1;
-        const bool table = x >= 0 && sx > 1;
-        const int* gv = a.G + (long long)v * a.kp;
-        int rc = 0, ex = 0, ub = 0, nq = 0;
-        if (single) rc = row_part(a, u, v, l, gs);
-        if (table) summary_part(a, gv, x, l, gs, ex, ub, nq);
-        rc = group_sum(rc, gs);
-        ex = group_sum(ex, gs);
-        ub = group_sum(ub, gs);
-        const bool open = table && 2 * (Aa - k - ub) - k * (sa - 1 - sx) < 0;
-        int pb = 0;
-        if (open) pb = probe_part(a, a.table, mask, gv, x, l, gs);
-        pb = group_sum(pb, gs);
-        if ((single || open) && l == 0) {
-            const int A = single ? rc - pad : ex + pb;
-            const int dD = 2 * (Aa - k - A) - k * (sa - 1 - sx);
-            if (dD < 0) atomicMin(&a.best[v], pack_key(dD, x));
+        const unsigned long long pair = x >= 0 ? ((unsigned long long)(unsigned)v << 32) | (unsigned)x : kEmpty;
+        const unsigned same = __match_any_sync(kFull, pair);
+        const bool keep = x >= 0 && (__ffs(same) - 1) == lane;
+        const unsigned km = __ballot_sync(kFull, keep);
+        if (keep) {
+            const int p = __popc(km & lt);
+            const int cv = __ldg(a.C + v);
+            es.v[p] = v;
+            es.u[p] = u;
+            es.x[p] = x;
+            es.sx[p] = __ldg(a.size + x);
+            es.sa[p] = __ldg(a.size + cv);
+            es.Aa[p] = __ldg(a.aown + v);
         }
+        __syncwarp();
+        const int nf = __popc(km);
+        for (int r0 = 0; r0 < nf; r0 += per) {
+            const int j = r0 + lane / gs;
+            const bool valid = j < nf;
+            const int ev = valid ? es.v[j] : 0, eu = valid ? es.u[j] : 0, ex_ = valid ? es.x[j] : 0;
+            const int sx = valid ? es.sx[j] : 0, sa = valid ? es.sa[j] : 0, Aa = valid ? es.Aa[j] : 0;
+            const bool single = valid && sx == 1;
+            const bool table = valid && sx > 1;
+            const int* gv = a.G + (long long)ev * a.kp;
+            int rc = 0, ex = 0, ub = 0, nq = 0;
+            if (single) rc = row_part(a, eu, ev, l, gs);
+            if (table) summary_part(a, gv, ex_, l, gs, ex, ub, nq);
+            rc = group_sum(rc, gs);
+            ex = group_sum(ex, gs);
+            ub = group_sum(ub, gs);
+            const bool open = table && 2 * (Aa - k - ub) - k * (sa - 1 - sx) < 0;
+            int pb = 0;
+            if (open) pb = probe_part(a, a.table, mask, gv, ex_, l, gs);
+            pb = group_sum(pb, gs);
+            if ((single || open) && l == 0) {
+                const int A = single ? rc - pad : ex + pb;
+                const int dD = 2 * (Aa - k - A) - k * (sa - 1 - sx);
+                if (dD < 0) atomicMin(&a.best[ev], pack_key(dD, ex_));
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -399,28 +424,20 @@ __global__ void k_h_apply(SweepArgs a, int undo)
     }
 }
 
-// F' = k sum_c s_c^2 - 2 sum_keys n^2 (+ sum_ij |P_ij|^2, added in k_h_decide)
-// from the rebuilt table.
+// F' = k sum_c s_c^2 - 2 sum_keys n^2 (+ sum_ij |P_ij|^2, added in k_h_decide):
+// the table part was added by the summary pass of the rebuild, this adds the
+// size part.
 __global__ void k_h_eval(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip || !st->heavy || st->err) return;
-    const unsigned long long mask = st->mask;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    const unsigned long long work = mask + 1 > (unsigned long long)a.n ? mask + 1 : (unsigned long long)a.n;
-    for (unsigned long long b0 = (unsigned long long)blockIdx.x * blockDim.x; b0 < work; b0 += stride) {
-        const unsigned long long t = b0 + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < a.n; b0 += stride) {
+        const long long t = b0 + threadIdx.x;
         long long acc = 0;
-        if (t < (unsigned long long)a.n) {
+        if (t < a.n) {
             const long long sz = a.size[t];
-            acc += (long long)a.k * sz * sz;
-        }
-        if (t <= mask) {
-            const ulonglong2 e = reinterpret_cast<const ulonglong2*>(a.table)[t];
-            if (e.x != kEmpty) {
-                const long long c = (int)(unsigned)(e.y & 0xffffffffull);
-                acc -= 2 * c * c;
-            }
+            acc = (long long)a.k * sz * sz;
         }
         block_add64(acc, &st->recompute);
     }
@@ -748,15 +765,16 @@ __global__ void k_end(SweepArgs a)
     st->sweeps += 1;
     st->run_sweeps += 1;
     if (st->nprop == 0 || st->run_sweeps >= st->run_limit) st->stop = 1;
-    // compaction: rebuild when occupied slots pass one half (dead keys), or
-    // shrink when the live keys fill less than one sixth of the capacity.  The
-    // new capacity holds the live keys plus half of k x (moves of this sweep),
-    // a forecast of the next sweep's new keys, at load <= 1/2.
+    // compaction: rebuild without the dead keys when occupied slots pass one
+    // half of the capacity; the new capacity holds the live keys plus k x
+    // (moves of this sweep), a forecast of the next sweep's new keys, at load
+    // <= 1/2.  (Summary rows settle most of each score, so a table larger than
+    // needed costs little; it is not shrunk otherwise.)
     const unsigned long long live = (unsigned long long)st->live;
-    const unsigned long long want = 2 * live + (st->heavy ? 0ull : (unsigned long long)a.k * st->moves);
+    const unsigned long long want = 2 * (live + (unsigned long long)a.k * st->moves);
     unsigned long long c = a.cap_min;
     while (c < want && c < a.mask_max + 1) c <<= 1;
-    if (st->tvalid && (st->used > cap / 2 || (live * 6 < cap && c < cap))) {
+    if (st->tvalid && st->used > cap / 2) {
         st->new_mask = c - 1;
         st->rebuild = 1;
     } else {
