@@ -58,8 +58,9 @@ typedef struct {
                                default 20 */
     int32_t debug_checks;   /* 1: after every sweep recompute F from scratch on the device and
                                fail with CC_ERR_INVALID if it differs from the incremental F */
-    int32_t table_log2;     /* log2 of the allocated contingency hash capacity; 0 = automatic
-                               (>= 4 k n slots of 16 bytes) */
+    int32_t table_log2;     /* log2 of the allocated contingency hash capacity (slots of 16
+                               bytes); 0 = automatic: the least power of two >= 2 k n + 64
+                               (>= 4 k n + 64 with sweep_mode 1) */
     int32_t table_start_log2; /* log2 of the capacity in use at the singleton start; 0 =
                                automatic (>= 2 k n).  The capacity in use then follows the
                                live keys; a sweep that would fill it is abandoned before
@@ -67,7 +68,9 @@ typedef struct {
     int32_t sweep_mode;     /* how a sweep evaluates dF of its kept moves P1 (the results are
                                identical): 0 = automatic (a rebuild of the contingency hash
                                from the tentatively moved consensus when more than n/8
-                               vertices propose, otherwise staged count deltas); 1 = always
+                               vertices propose -- in a batch, when the proposals carry more
+                               than 1/8 of all label rows -- otherwise staged count
+                               deltas); 1 = always
                                staged deltas (the hash is built at the singleton start);
                                2 = always a rebuild */
     int32_t reserved[3];    /* must be zero */
@@ -136,6 +139,47 @@ cc_status cc_create_dev(int32_t n, int64_t nnz, const int64_t* row_off_dev, cons
                         int32_t k, const int32_t* labels_dev, const cc_options* opt, void* stream,
                         cc_ctx** out);
 
+/* One job of a batch: the arguments of cc_create for that job (host memory). */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int64_t* row_off;
+    const int32_t* col;
+    int32_t k;
+    const int32_t* labels;
+} cc_job_desc;
+
+/* Creates one context for `jobs` independent consensus jobs (the batched
+ * form: many small problems solved together).  Each job follows the rules of
+ * cc_create; the jobs are held on the device as one disjoint union (job j's
+ * vertices follow those of jobs 0..j-1) and every sweep runs all of them in
+ * the same kernel launches.  Each job keeps its own guard decisions,
+ * objective, stopping condition and history, so its results are those of
+ * running it alone in its own context.  A run stops when every job has
+ * stopped (a job stops on a sweep with no proposal or at the sweep limit).
+ * Per-job results: cc_job_objective, cc_job_history, cc_job_labels.
+ * cc_consensus_labels / cc_cluster_ids / cc_set_cluster_ids work on all jobs
+ * at once: int32[sum n_j], job after job, ids and labels local to each job.
+ * cc_sweep (info must be NULL), cc_history, cc_objective and
+ * cc_objective_recompute need a single-job context (else CC_ERR_INVALID).
+ * Errors as cc_create; a message names the first job that failed. */
+cc_status cc_batch_create(int32_t jobs, const cc_job_desc* descs, const cc_options* opt, cc_ctx** out);
+
+/* Number of jobs of the context (1 for cc_create / cc_create_dev). */
+cc_status cc_job_count(const cc_ctx* ctx, int32_t* out);
+
+/* F of job `job` (ordered pairs, as cc_objective) and, if sweeps is not NULL,
+ * the number of sweeps recorded for it since creation or the last reset. */
+cc_status cc_job_objective(cc_ctx* ctx, int32_t job, int64_t* out, int32_t* sweeps);
+
+/* The sweep records of job `job`, as cc_history.  A batch context keeps the
+ * last max(64, max_sweeps option) records per job; a single-job one 65536. */
+cc_status cc_job_history(cc_ctx* ctx, int32_t job, int32_t max, cc_sweep_info* out, int32_t* count);
+
+/* The consensus of job `job` as int32[n_j] host, renumbered as by
+ * cc_consensus_labels of that job alone. */
+cc_status cc_job_labels(cc_ctx* ctx, int32_t job, int32_t* out);
+
 /* Uses the given cudaStream_t (NULL: the context's own) for later calls. */
 cc_status cc_set_stream(cc_ctx* ctx, void* stream);
 
@@ -153,7 +197,8 @@ cc_status cc_reset(cc_ctx* ctx);
 cc_status cc_set_cluster_ids(cc_ctx* ctx, const int32_t* C);
 
 /* Runs one synchronous sweep (Parallel algorithm section) and, if info is not
- * NULL, writes its record.  A sweep with no proposal changes nothing.
+ * NULL, writes its record (info must be NULL for a batch).  A sweep with no
+ * proposal changes nothing.
  * Errors: CC_ERR_TABLE_FULL, CC_ERR_CUDA, CC_ERR_INVALID (debug check). */
 cc_status cc_sweep(cc_ctx* ctx, cc_sweep_info* info);
 
@@ -182,26 +227,31 @@ cc_status cc_table_stats(cc_ctx* ctx, cc_table_info* out);
 cc_status cc_launch_count(const cc_ctx* ctx, int64_t* out);
 
 /* Copies the records of the sweeps run since creation or the last reset,
- * oldest first: at most max entries into out, the total count into *count. */
+ * oldest first: at most max entries into out, the total count into *count.
+ * Single-job contexts only (batches: cc_job_history). */
 cc_status cc_history(cc_ctx* ctx, int32_t max, cc_sweep_info* out, int32_t* count);
 
 /* F(C) = sum_i Mirkin(C, P_i), ordered pairs (Eq. objective1), as kept
- * incrementally by the sweeps. */
+ * incrementally by the sweeps.  Single-job contexts only (cc_job_objective). */
 cc_status cc_objective(cc_ctx* ctx, int64_t* out);
 
 /* F(C) recomputed from scratch on the device from C and the labels
- * (k sum_c |c|^2 + sum_ij |P_ij|^2 - 2 sum_{c,i,j} n(c,i,j)^2), for checks. */
+ * (k sum_c |c|^2 + sum_ij |P_ij|^2 - 2 sum_{c,i,j} n(c,i,j)^2), for checks.
+ * Single-job contexts only. */
 cc_status cc_objective_recompute(cc_ctx* ctx, int64_t* out);
 
 /* The consensus as int32[n] (caller-allocated host buffer), clusters
  * renumbered 0..b-1 in order of first appearance by vertex index. */
 cc_status cc_consensus_labels(cc_ctx* ctx, int32_t* out);
 
-/* The raw cluster ids (founding vertices) as int32[n] host, for parity checks. */
+/* The raw cluster ids (founding vertices) as int32[n] host, for parity checks.
+ * A batch gives int32[sum n_j], each job's ids local to the job. */
 cc_status cc_cluster_ids(cc_ctx* ctx, int32_t* out);
 
 /* Device pointer to the context's int32[n] cluster-id array (valid until the
- * next call that modifies the context or cc_destroy); for zero-copy readers. */
+ * next call that modifies the context or cc_destroy); for zero-copy readers.
+ * In a batch the ids are those of the union: job j's ids are offset by the
+ * number of vertices of jobs 0..j-1. */
 cc_status cc_cluster_ids_dev(cc_ctx* ctx, const int32_t** out);
 
 /* Message of the last failure on this context ("" if none).  Owned by the
@@ -211,6 +261,83 @@ const char* cc_last_error(const cc_ctx* ctx);
 
 /* Frees every resource of the context.  NULL is allowed. */
 void cc_destroy(cc_ctx* ctx);
+
+/* Device bytes a context for these jobs would hold (*persistent, until
+ * cc_destroy) and at most during its creation (*peak), computed on the host
+ * from n, nnz and k of each job and the options (the data pointers of the
+ * descriptors are not read and may be NULL).  Either output may be NULL.
+ * Errors: those of cc_batch_create's size and option checks. */
+cc_status cc_estimate_bytes(int32_t jobs, const cc_job_desc* descs, const cc_options* opt, int64_t* persistent,
+                            int64_t* peak);
+
+/* ---- served form: a request loop with continuous batching ---------------
+ * A server takes consensus jobs as they arrive and keeps them resident on
+ * the GPU while they run.  Waiting jobs are admitted in arrival order into
+ * contexts of many jobs (as cc_batch_create) while a context slot is free and
+ * the new context's device bytes (cc_estimate_bytes, peak) fit in what the
+ * budget has left; the oldest waiting job opens a context and later ones of
+ * the same lane bin (k in the same range: 1..5, 6..10, 11..20, 21..40,
+ * 41..80, above 80) join it while they fit.  Every context runs on its
+ * own stream, so contexts admitted while others run overlap with them on the
+ * device.  A job's results are those of running it alone.  Single-threaded:
+ * all calls on one server come from one thread at a time.  Device memory
+ * comes from a memory pool of the server (stream-ordered allocation). */
+typedef struct cc_server cc_server;
+
+typedef struct {
+    int64_t budget_bytes;   /* device bytes the server may hold for contexts; 0 = 80% of the
+                               free device memory at creation */
+    int32_t max_active;     /* contexts in flight at once (1..64); 0 = 4 */
+    int32_t max_batch_jobs; /* jobs admitted into one context; 0 = 256 */
+    int32_t reserved[4];    /* must be zero */
+} cc_server_options;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed;
+    int64_t batches;        /* contexts created */
+    int64_t max_in_flight;  /* most contexts in flight at once */
+    int64_t in_flight, queued;
+    int64_t budget_bytes, bytes_in_use, peak_bytes;
+} cc_server_info;
+
+/* Fills *o with the defaults above. */
+void cc_server_default_options(cc_server_options* o);
+
+/* Creates a server on the current device.  opt: options of every job
+ * (max_sweeps is each job's sweep limit), or NULL for the defaults. */
+cc_status cc_server_create(const cc_server_options* sopt, const cc_options* opt, cc_server** out);
+
+/* Queues one job (host arrays as in cc_create) and returns at once with its
+ * ticket.  Unlike the other calls, the job's arrays are borrowed until the
+ * job is done: they must stay valid and unchanged until then.  labels_out
+ * (int32[n], host) receives the job's consensus, renumbered as by
+ * cc_consensus_labels.  Errors: the size checks of cc_create. */
+cc_status cc_server_submit(cc_server* s, const cc_job_desc* job, int32_t* labels_out, int64_t* ticket);
+
+/* Advances the server: harvests the contexts whose jobs have all stopped,
+ * queues the next graph launch of those still running and admits waiting
+ * jobs.  wait != 0: if nothing finished and nothing was admitted, keeps
+ * polling (at most about a second) until something does.  Up to max_done
+ * tickets of jobs done since the last report are written to done (*n_done
+ * of them); *pending = jobs submitted and not yet done.  A job that fails
+ * is done with a non-zero status (cc_server_job). */
+cc_status cc_server_progress(cc_server* s, int32_t wait, int64_t* done, int32_t max_done, int32_t* n_done,
+                             int64_t* pending);
+
+/* State of a job: *done = 1 once its labels are written; its objective
+ * (ordered pairs), sweeps run and cc_status.  Records are kept until
+ * cc_server_destroy. */
+cc_status cc_server_job(cc_server* s, int64_t ticket, int32_t* done, int64_t* F, int32_t* sweeps,
+                        int32_t* status);
+
+cc_status cc_server_stats(const cc_server* s, cc_server_info* out);
+
+/* Message of the last failure on the server (NULL: of the last failed
+ * cc_server_create in this thread). */
+const char* cc_server_last_error(const cc_server* s);
+
+/* Waits for the work in flight and frees everything.  NULL is allowed. */
+void cc_server_destroy(cc_server* s);
 
 /* ---- allocation-free output renumbering --------------------------------
  * The paper has no counterpart to this call; it serves callers of the

@@ -23,6 +23,9 @@ STATUS_NAMES = {0: "CC_OK", 1: "CC_ERR_INVALID", 2: "CC_ERR_OOM", 3: "CC_ERR_CUD
 EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", "cc_reset", "cc_set_cluster_ids", "cc_sweep",
            "cc_run_until_converged", "cc_last_run_timing", "cc_table_stats", "cc_launch_count", "cc_history", "cc_objective", "cc_objective_recompute",
            "cc_consensus_labels", "cc_cluster_ids", "cc_cluster_ids_dev", "cc_last_error", "cc_destroy",
+           "cc_batch_create", "cc_job_count", "cc_job_objective", "cc_job_history", "cc_job_labels",
+           "cc_estimate_bytes", "cc_server_default_options", "cc_server_create", "cc_server_submit",
+           "cc_server_progress", "cc_server_job", "cc_server_stats", "cc_server_last_error", "cc_server_destroy",
            "cc_renumber_noalloc")
 
 # Largest n accepted by cc_renumber_noalloc (its built-in scratch holds 2 n ints).
@@ -52,6 +55,25 @@ class cc_table_info(ctypes.Structure):
 class cc_sweep_info(ctypes.Structure):
     _fields_ = [("proposals", ctypes.c_int64), ("p1", ctypes.c_int64), ("dF_p1", ctypes.c_int64),
                 ("fallback", ctypes.c_int64), ("moves", ctypes.c_int64), ("F", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class cc_job_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_off", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("k", ctypes.c_int32), ("labels", ctypes.c_void_p)]
+
+
+class cc_server_options(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("max_batch_jobs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class cc_server_info(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "admitted", "completed", "failed", "batches",
+                                              "max_in_flight", "in_flight", "queued", "budget_bytes",
+                                              "bytes_in_use", "peak_bytes")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -103,6 +125,36 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cc_last_error.argtypes = [P]
     lib.cc_destroy.restype = None
     lib.cc_destroy.argtypes = [P]
+    lib.cc_batch_create.restype = c.c_int
+    lib.cc_batch_create.argtypes = [c.c_int32, c.POINTER(cc_job_desc), c.POINTER(cc_options), c.POINTER(P)]
+    lib.cc_job_count.restype = c.c_int
+    lib.cc_job_count.argtypes = [P, c.POINTER(c.c_int32)]
+    lib.cc_job_objective.restype = c.c_int
+    lib.cc_job_objective.argtypes = [P, c.c_int32, c.POINTER(c.c_int64), c.POINTER(c.c_int32)]
+    lib.cc_job_history.restype = c.c_int
+    lib.cc_job_history.argtypes = [P, c.c_int32, c.c_int32, c.POINTER(cc_sweep_info), c.POINTER(c.c_int32)]
+    lib.cc_job_labels.restype = c.c_int
+    lib.cc_job_labels.argtypes = [P, c.c_int32, P]
+    lib.cc_estimate_bytes.restype = c.c_int
+    lib.cc_estimate_bytes.argtypes = [c.c_int32, c.POINTER(cc_job_desc), c.POINTER(cc_options),
+                                      c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
+    lib.cc_server_default_options.restype = None
+    lib.cc_server_default_options.argtypes = [c.POINTER(cc_server_options)]
+    lib.cc_server_create.restype = c.c_int
+    lib.cc_server_create.argtypes = [c.POINTER(cc_server_options), c.POINTER(cc_options), c.POINTER(P)]
+    lib.cc_server_submit.restype = c.c_int
+    lib.cc_server_submit.argtypes = [P, c.POINTER(cc_job_desc), P, c.POINTER(c.c_int64)]
+    lib.cc_server_progress.restype = c.c_int
+    lib.cc_server_progress.argtypes = [P, c.c_int32, P, c.c_int32, c.POINTER(c.c_int32), c.POINTER(c.c_int64)]
+    lib.cc_server_job.restype = c.c_int
+    lib.cc_server_job.argtypes = [P, c.c_int64, c.POINTER(c.c_int32), c.POINTER(c.c_int64), c.POINTER(c.c_int32),
+                                  c.POINTER(c.c_int32)]
+    lib.cc_server_stats.restype = c.c_int
+    lib.cc_server_stats.argtypes = [P, c.POINTER(cc_server_info)]
+    lib.cc_server_last_error.restype = c.c_char_p
+    lib.cc_server_last_error.argtypes = [P]
+    lib.cc_server_destroy.restype = None
+    lib.cc_server_destroy.argtypes = [P]
     lib.cc_renumber_noalloc.restype = c.c_int
     lib.cc_renumber_noalloc.argtypes = [c.c_int32, P, P, P]
     return lib
@@ -155,6 +207,56 @@ def cc_create_dev(n: int, nnz: int, row_off_ptr: int, col_ptr: int, k: int, labe
     return ctx
 
 
+def cc_batch_create(jobs, options: cc_options | None = None):
+    """jobs: sequence of (row_off int64[n+1], col int32[nnz], labels int32[k, n]) host arrays -> ctx handle."""
+    keep = []
+    descs = (cc_job_desc * max(len(jobs), 1))()
+    for j, (row_off, col, labels) in enumerate(jobs):
+        row_off = np.ascontiguousarray(row_off, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        labels = np.ascontiguousarray(labels, dtype=np.int32)
+        if labels.ndim != 2:
+            raise ValueError(f"job {j}: labels must be int32[k, n]")
+        k, n = labels.shape
+        if len(row_off) != n + 1:
+            raise ValueError(f"job {j}: row_off must have n + 1 entries")
+        keep += [row_off, col, labels]
+        descs[j] = cc_job_desc(n, len(col), _ptr(row_off).value, _ptr(col).value, k, _ptr(labels).value)
+    ctx = ctypes.c_void_p()
+    st = lib.cc_batch_create(len(jobs), descs, ctypes.byref(options) if options is not None else None,
+                             ctypes.byref(ctx))
+    _check(st, None)
+    return ctx
+
+
+def cc_job_count(ctx) -> int:
+    out = ctypes.c_int32(0)
+    _check(lib.cc_job_count(ctx, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def cc_job_objective(ctx, job: int):
+    """(F, sweeps recorded) of one job."""
+    out = ctypes.c_int64(0)
+    sw = ctypes.c_int32(0)
+    _check(lib.cc_job_objective(ctx, job, ctypes.byref(out), ctypes.byref(sw)), ctx)
+    return out.value, sw.value
+
+
+def cc_job_history(ctx, job: int) -> list:
+    count = ctypes.c_int32(0)
+    _check(lib.cc_job_history(ctx, job, 0, None, ctypes.byref(count)), ctx)
+    buf = (cc_sweep_info * max(count.value, 1))()
+    _check(lib.cc_job_history(ctx, job, count.value, buf, ctypes.byref(count)), ctx)
+    return [buf[i].as_dict() for i in range(min(count.value, len(buf)))]
+
+
+def cc_job_labels(ctx, job: int, n: int, out: np.ndarray | None = None) -> np.ndarray:
+    out = np.empty(n, np.int32) if out is None else out
+    _check(lib.cc_job_labels(ctx, job, _ptr(out)), ctx)
+    return out
+
+
 def cc_set_stream(ctx, stream: int = 0):
     _check(lib.cc_set_stream(ctx, ctypes.c_void_p(stream or None)), ctx)
 
@@ -168,10 +270,14 @@ def cc_set_cluster_ids(ctx, C):
     _check(lib.cc_set_cluster_ids(ctx, _ptr(C)), ctx)
 
 
-def cc_sweep(ctx) -> dict:
-    info = cc_sweep_info()
-    _check(lib.cc_sweep(ctx, ctypes.byref(info)), ctx)
-    return info.as_dict()
+def cc_sweep(ctx, info: bool = True) -> dict | None:
+    """One sweep; its record for a single-job context (info=False for a batch)."""
+    if not info:
+        _check(lib.cc_sweep(ctx, None), ctx)
+        return None
+    rec = cc_sweep_info()
+    _check(lib.cc_sweep(ctx, ctypes.byref(rec)), ctx)
+    return rec.as_dict()
 
 
 def cc_run_until_converged(ctx, max_sweeps: int = 0) -> int:
@@ -253,3 +359,85 @@ def cc_renumber_noalloc(n: int, ids_ptr: int, labels_ptr: int, stream: int = 0):
     """Renumbers n device ids (ids_ptr) into labels_ptr without allocating device memory."""
     _check(lib.cc_renumber_noalloc(n, ctypes.c_void_p(ids_ptr), ctypes.c_void_p(labels_ptr),
                                    ctypes.c_void_p(stream or None)), None)
+
+
+def _job_desc(row_off, col, labels, keep):
+    row_off = np.ascontiguousarray(row_off, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    if labels.ndim != 2:
+        raise ValueError("labels must be int32[k, n]")
+    k, n = labels.shape
+    if len(row_off) != n + 1:
+        raise ValueError("row_off must have n + 1 entries")
+    keep += [row_off, col, labels]
+    return cc_job_desc(n, len(col), _ptr(row_off).value, _ptr(col).value, k, _ptr(labels).value)
+
+
+def cc_estimate_bytes(sizes, options: cc_options | None = None):
+    """sizes: sequence of (n, nnz, k) -> (persistent bytes, peak bytes) of a context for those jobs."""
+    descs = (cc_job_desc * max(len(sizes), 1))()
+    for j, (n, nnz, k) in enumerate(sizes):
+        descs[j] = cc_job_desc(n, nnz, None, None, k, None)
+    a = ctypes.c_int64(0)
+    b = ctypes.c_int64(0)
+    _check(lib.cc_estimate_bytes(len(sizes), descs, ctypes.byref(options) if options is not None else None,
+                                 ctypes.byref(a), ctypes.byref(b)), None)
+    return a.value, b.value
+
+
+def _check_server(status: int, srv=None):
+    if status != CC_OK:
+        msg = lib.cc_server_last_error(srv)
+        raise CCError(status, msg.decode() if msg else "")
+
+
+def cc_server_default_options() -> cc_server_options:
+    o = cc_server_options()
+    lib.cc_server_default_options(ctypes.byref(o))
+    return o
+
+
+def cc_server_create(server_options: cc_server_options | None = None, options: cc_options | None = None):
+    srv = ctypes.c_void_p()
+    st = lib.cc_server_create(ctypes.byref(server_options) if server_options is not None else None,
+                              ctypes.byref(options) if options is not None else None, ctypes.byref(srv))
+    _check_server(st, None)
+    return srv
+
+
+def cc_server_submit(srv, desc: cc_job_desc, out: np.ndarray) -> int:
+    """desc: a cc_job_desc whose arrays the caller keeps alive until the job is done; out: int32[n]."""
+    t = ctypes.c_int64(0)
+    _check_server(lib.cc_server_submit(srv, ctypes.byref(desc), _ptr(out), ctypes.byref(t)), srv)
+    return t.value
+
+
+def cc_server_progress(srv, wait: bool = False, max_done: int = 4096):
+    """-> (tickets done since the last report, jobs pending)."""
+    buf = np.empty(max_done, np.int64)
+    nd = ctypes.c_int32(0)
+    pend = ctypes.c_int64(0)
+    _check_server(lib.cc_server_progress(srv, 1 if wait else 0, _ptr(buf), max_done, ctypes.byref(nd),
+                                         ctypes.byref(pend)), srv)
+    return buf[: nd.value].tolist(), pend.value
+
+
+def cc_server_job(srv, ticket: int) -> dict:
+    done = ctypes.c_int32(0)
+    F = ctypes.c_int64(0)
+    sw = ctypes.c_int32(0)
+    st = ctypes.c_int32(0)
+    _check_server(lib.cc_server_job(srv, ticket, ctypes.byref(done), ctypes.byref(F), ctypes.byref(sw),
+                                    ctypes.byref(st)), srv)
+    return {"done": bool(done.value), "F": F.value, "sweeps": sw.value, "status": st.value}
+
+
+def cc_server_stats(srv) -> dict:
+    out = cc_server_info()
+    _check_server(lib.cc_server_stats(srv, ctypes.byref(out)), srv)
+    return out.as_dict()
+
+
+def cc_server_destroy(srv):
+    lib.cc_server_destroy(srv)

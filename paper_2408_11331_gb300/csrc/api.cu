@@ -1,67 +1,16 @@
-// The C ABI declared in include/cc.h: context lifetime, the sweep loop as a
-// captured CUDA graph, and the output calls.
+// The C ABI declared in include/cc.h: context lifetime (one job, or a batch of
+// jobs held as one disjoint union), the sweep loop as captured CUDA graphs,
+// and the output calls.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
 #include <vector>
 
-#include "cc_internal.cuh"
+#include "context.cuh"
 
 using namespace ccg;
-
-// A run of `limit` sweeps unrolled into one graph, with events at every sweep
-// boundary and around every proposal launch.
-struct RunGraph {
-    cudaGraphExec_t exec = nullptr;
-    std::vector<cudaEvent_t> bound;    // limit + 1
-    std::vector<cudaEvent_t> prop;     // 2 * limit
-};
-
-struct cc_ctx {
-    int n = 0, k = 0, kp = 0, lshift = 0;
-    long long nnz = 0;
-    int device = 0, sms = 0;
-    cudaStream_t stream = nullptr;      // stream used by calls
-    cudaStream_t own_stream = nullptr;  // stream created by the context (also used for capture)
-    long long* off = nullptr;
-    int* col = nullptr;
-    int* src = nullptr;                 // source vertex of each CSR entry
-    int* G = nullptr;
-    int* C = nullptr;
-    int* size = nullptr;
-    int* dsize = nullptr;
-    unsigned long long* best = nullptr;
-    int* aown = nullptr;                // A_a per vertex (proposal step)
-    Slot* table = nullptr;
-    int* pv = nullptr;
-    int* pa = nullptr;
-    int* pb = nullptr;
-    int* pg = nullptr;
-    unsigned char* pflag = nullptr;
-    unsigned int* pslot = nullptr;
-    int* scratch = nullptr;             // 3n + n/1024 + 64 ints for the output renumbering
-    int* members = nullptr;             // rebuild scratch (n)
-    int4* summ = nullptr;               // per-cluster label summaries (n x kp)
-    int* cursor = nullptr;              // rebuild scratch (n)
-    int* bsum = nullptr;                // rebuild scratch (n/1024 + 2)
-    DevState* st = nullptr;
-    cc_sweep_info* hist = nullptr;
-    int hist_cap = 1 << 16;
-    SweepArgs args{};
-    std::map<int, RunGraph> graphs;
-    std::vector<float> sweep_ms;        // device time of each sweep of the last run
-    std::vector<float> propose_ms;      // ... and of its proposal kernels
-    long long launches = 0;             // kernels launched so far
-    int grid = 0;
-    long long partition_sq = 0, F0 = 0;
-    unsigned long long cap_start = 0;   // active table capacity at the singleton start
-    unsigned long long cap_max = 0;     // allocated table capacity
-    bool started = false;               // start_state ran once
-    cc_options opt{};
-    std::vector<void*> allocs;
-    std::string err;
-};
 
 namespace {
 
@@ -91,9 +40,11 @@ template <typename T>
 cudaError_t dalloc(cc_ctx* c, T** p, size_t count)
 {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+    cudaError_t e = c->pool ? cudaMallocFromPoolAsync(&q, bytes, c->pool, c->own_stream) : cudaMalloc(&q, bytes);
     if (e != cudaSuccess) return e;
     c->allocs.push_back(q);
+    c->bytes += bytes;
     *p = static_cast<T*>(q);
     return cudaSuccess;
 }
@@ -110,8 +61,25 @@ void free_all(cc_ctx* c)
 {
     for (auto& kv : c->graphs) destroy_graph(kv.second);
     c->graphs.clear();
-    for (void* p : c->allocs) cudaFree(p);
+    if (c->pool) {
+        // stream-ordered: the memory returns to the pool once the context's
+        // queued work has finished, without waiting here
+        if (c->stream != c->own_stream) {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(ev, c->stream);
+                cudaStreamWaitEvent(c->own_stream, ev, 0);
+                cudaEventDestroy(ev);
+            }
+        }
+        for (void* p : c->allocs) cudaFreeAsync(p, c->own_stream);
+    } else {
+        for (void* p : c->allocs) cudaFree(p);
+    }
     c->allocs.clear();
+    c->bytes = 0;
+    if (c->chunk_done) cudaEventDestroy(c->chunk_done);
+    c->chunk_done = nullptr;
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     c->own_stream = nullptr;
 }
@@ -131,6 +99,14 @@ cc_status read_state(cc_ctx* c, DevState* out)
     return CC_OK;
 }
 
+cc_status read_jobs(cc_ctx* c, std::vector<JobState>& out)
+{
+    out.resize(c->jobs);
+    CC_CUDA(c, cudaMemcpyAsync(out.data(), c->js, sizeof(JobState) * c->jobs, cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CC_OK;
+}
+
 cc_status check_device_error(cc_ctx* c, const DevState& s)
 {
     if (s.err == CC_ERR_TABLE_FULL) return fail(c, CC_ERR_TABLE_FULL, "contingency hash is full");
@@ -139,27 +115,38 @@ cc_status check_device_error(cc_ctx* c, const DevState& s)
     return CC_OK;
 }
 
-cc_status objective_recompute(cc_ctx* c, long long* out)
+cc_status need_single(cc_ctx* c)
+{
+    if (c->jobs != 1) return fail(c, CC_ERR_INVALID, "this call needs a single-job context; use the cc_job_* calls");
+    return CC_OK;
+}
+
+// F of every job recomputed from scratch (the table is built first if the
+// context is still at the singleton start without one).
+cc_status objective_recompute(cc_ctx* c, std::vector<long long>& F)
 {
     DevState pre;
     cc_status rp = read_state(c, &pre);
     if (rp != CC_OK) return rp;
     if (!pre.tvalid) {
-        // no table yet (singleton start): build it from C first
         CC_CUDA(c, cudaMemcpyAsync(&c->st->new_mask, &pre.mask, sizeof(pre.mask), cudaMemcpyHostToDevice, c->stream));
-        CC_CUDA(c, launch_table_rebuild(c->args, false, c->stream));
+        CC_CUDA(c, launch_table_rebuild(c->args, c->rows, false, c->stream));
         c->launches += kKernelsPerRebuild;
     }
     CC_CUDA(c, launch_objective_recompute(c->args, c->stream));
-    c->launches += 1;
-    DevState s;
-    cc_status r = read_state(c, &s);
+    c->launches += 2;
+    std::vector<JobState> js;
+    cc_status r = read_jobs(c, js);
     if (r != CC_OK) return r;
-    *out = s.recompute + c->partition_sq;
-    return CC_OK;
+    F.resize(c->jobs);
+    for (int j = 0; j < c->jobs; ++j) F[j] = js[j].recompute + c->psq[j];
+    DevState s;
+    r = read_state(c, &s);
+    if (r != CC_OK) return r;
+    return check_device_error(c, s);
 }
 
-// Singleton start: C[v] = v, sizes 1, table rebuilt, F = F0, history cleared.
+// Singleton start of every job: C[v] = v, sizes 1, F = F0, history cleared.
 cc_status start_state(cc_ctx* c)
 {
     DevState s;
@@ -172,21 +159,27 @@ cc_status start_state(cc_ctx* c)
         s.retries = prev.retries;
     }
     c->started = true;
-    s.partition_sq = c->partition_sq;
-    s.F = c->F0;
     s.stop = 1;
     s.new_mask = c->cap_start - 1;
     s.mask = c->cap_start - 1;
+    std::vector<JobState> js(c->jobs);
+    for (int j = 0; j < c->jobs; ++j) {
+        std::memset(&js[j], 0, sizeof(JobState));
+        js[j].F = c->F0[j];
+        js[j].partition_sq = c->psq[j];
+        js[j].stop = 1;
+    }
     CC_CUDA(c, cudaMemcpyAsync(c->st, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
+    CC_CUDA(c, cudaMemcpyAsync(c->js, js.data(), sizeof(JobState) * c->jobs, cudaMemcpyHostToDevice, c->stream));
     CC_CUDA(c, launch_init_state(c->args, c->stream));
     if (c->opt.sweep_mode == 1) {
         // staged deltas need the singleton counts in the table from the start
-        CC_CUDA(c, launch_table_rebuild(c->args, false, c->stream));
+        CC_CUDA(c, launch_table_rebuild(c->args, c->rows, false, c->stream));
         c->launches += 1 + kKernelsPerRebuild;
     } else {
         // the first sweep rebuilds the table itself (it is always heavy);
         // the summary rows of singletons follow from the label rows
-        CC_CUDA(c, launch_singleton_summaries(c->args, c->stream));
+        CC_CUDA(c, launch_singleton_summaries(c->args, c->rows, c->stream));
         c->launches += 2;
     }
     DevState r;
@@ -202,10 +195,6 @@ cc_status ensure_graph(cc_ctx* c, int limit, RunGraph** out)
         *out = &it->second;
         return CC_OK;
     }
-    if (c->graphs.size() >= 8) {  // keep a few limits; drop the others
-        for (auto& kv : c->graphs) destroy_graph(kv.second);
-        c->graphs.clear();
-    }
     RunGraph g;
     g.bound.resize((size_t)limit + 1);
     g.prop.resize(2 * (size_t)limit);
@@ -216,7 +205,8 @@ cc_status ensure_graph(cc_ctx* c, int limit, RunGraph** out)
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < limit && e == cudaSuccess; ++s) {
         e = cudaEventRecordWithFlags(g.bound[s], c->own_stream, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = launch_sweep(c->args, c->grid, c->own_stream, g.prop[2 * s], g.prop[2 * s + 1]);
+        if (e == cudaSuccess)
+            e = launch_sweep(c->args, c->rows, c->grid, c->own_stream, g.prop[2 * s], g.prop[2 * s + 1]);
     }
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(g.bound[limit], c->own_stream, cudaEventRecordExternal);
     cudaError_t e2 = cudaStreamEndCapture(c->own_stream, &graph);
@@ -239,16 +229,17 @@ cc_status ensure_graph(cc_ctx* c, int limit, RunGraph** out)
 
 // Sweeps per graph launch: a run launches the graph until the device says the
 // run has stopped, so at most kChunk - 1 skipped sweep bodies are submitted
-// after the last sweep (each costs its kernels' launch latency).
+// after the last sweep.
 constexpr int kChunk = 4;
 
+// Runs every job until it stops; *done = largest number of sweeps of a job in this run.
 cc_status run(cc_ctx* c, int limit, int* done)
 {
     const int chunk = limit < kChunk ? limit : kChunk;
     RunGraph* g = nullptr;
     cc_status r = ensure_graph(c, chunk, &g);
     if (r != CC_OK) return r;
-    CC_CUDA(c, launch_run_begin(c->st, limit, c->stream));
+    CC_CUDA(c, launch_run_begin(c->args, limit, c->stream));
     c->launches += 1;
     c->sweep_ms.clear();
     c->propose_ms.clear();
@@ -261,7 +252,7 @@ cc_status run(cc_ctx* c, int limit, int* done)
         c->launches += (long long)chunk * kKernelsPerSweep;
         r = read_state(c, &st);
         if (r != CC_OK) return r;
-        const int ran = st.run_sweeps - before;
+        const int ran = st.run_bodies - before;
         for (int b = 0; b < ran && b < chunk; ++b) {
             float x = 0.f, y = 0.f;
             CC_CUDA(c, cudaEventElapsedTime(&x, g->bound[b], g->bound[b + 1]));
@@ -269,52 +260,154 @@ cc_status run(cc_ctx* c, int limit, int* done)
             c->sweep_ms.push_back(x);
             c->propose_ms.push_back(y);
         }
-        before = st.run_sweeps;
+        before = st.run_bodies;
         if (st.stop || st.err) break;
     }
     r = check_device_error(c, st);
     if (r != CC_OK) return r;
     if (!st.stop) return fail(c, CC_ERR_TABLE_FULL, "sweep retries did not converge");
-    if (done) *done = st.run_sweeps;
+    std::vector<JobState> js;
+    r = read_jobs(c, js);
+    if (r != CC_OK) return r;
+    int most = 0;
+    for (const JobState& s : js) most = std::max(most, s.run_sweeps);
+    if (done) *done = most;
     if (c->opt.debug_checks) {
-        long long F = 0;
-        r = objective_recompute(c, &F);
+        std::vector<long long> F;
+        r = objective_recompute(c, F);
         if (r != CC_OK) return r;
-        if (F != st.F) return fail(c, CC_ERR_INVALID, "debug check: incremental objective differs from recomputed");
+        for (int j = 0; j < c->jobs; ++j)
+            if (F[j] != js[j].F) return fail(c, CC_ERR_INVALID, "debug check: incremental objective differs from recomputed");
     }
     return CC_OK;
 }
 
-cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const int32_t* col, int32_t k,
-                        const int32_t* labels, bool on_device, const cc_options* opt, void* stream,
-                        cc_ctx** out)
+// Device bytes of one allocation of `bytes` (allocations are rounded up to
+// 512 bytes or more).
+inline size_t rounded(size_t bytes)
+{
+    return (std::max<size_t>(bytes, 16) + 511) & ~size_t(511);
+}
+
+}  // namespace
+
+namespace ccg {
+
+cc_options resolve_options(const cc_options* opt)
+{
+    cc_options o;
+    if (opt) o = *opt;
+    else cc_default_options(&o);
+    if (o.max_sweeps <= 0) o.max_sweeps = 20;
+    return o;
+}
+
+cc_status plan_jobs(int jobs, const JobInput* in, const cc_options& opt, Plan* out, std::string* msg)
+{
+    auto bad = [&](cc_status code, const std::string& m) {
+        *msg = m;
+        return code;
+    };
+    if (jobs < 1) return bad(CC_ERR_INVALID, "at least one job is needed");
+    if (!in) return bad(CC_ERR_INVALID, "job descriptors are NULL");
+    Plan p;
+    p.jobs = jobs;
+    for (int j = 0; j < jobs; ++j) {
+        const JobInput& q = in[j];
+        const std::string who = jobs > 1 ? "job " + std::to_string(j) + ": " : "";
+        if (q.n < 1) return bad(CC_ERR_INVALID, who + "n must be >= 1");
+        if (q.k < 1) return bad(CC_ERR_INVALID, who + "k must be >= 1");
+        if (q.k > 4096) return bad(CC_ERR_INVALID, who + "k must be <= 4096");
+        if (q.nnz < 0) return bad(CC_ERR_INVALID, who + "nnz must be >= 0");
+        if (3LL * q.k * q.n + q.k >= (1LL << 31)) return bad(CC_ERR_OVERFLOW, who + "3 k n + k >= 2^31");
+        p.n += q.n;
+        p.nnz += q.nnz;
+        p.rows += (long long)q.n * ((q.k + 3) & ~3);
+        p.keys += (long long)q.n * q.k;
+        p.parts += q.k;
+        p.kmax = std::max(p.kmax, (int)q.k);
+    }
+    if (p.n >= (1LL << 31)) return bad(CC_ERR_OVERFLOW, "more than 2^31 - 1 vertices in all jobs together");
+    cc_status r = check_options(opt, msg);
+    if (r != CC_OK) return r;
+    finish_plan(p, opt);
+    *out = p;
+    return CC_OK;
+}
+
+cc_status check_options(const cc_options& opt, std::string* msg)
+{
+    auto bad = [&](cc_status code, const std::string& m) {
+        *msg = m;
+        return code;
+    };
+    for (int r : opt.reserved)
+        if (r != 0) return bad(CC_ERR_INVALID, "reserved option fields must be zero");
+    if (opt.table_log2 < 0 || opt.table_log2 > 40) return bad(CC_ERR_INVALID, "table_log2 out of range");
+    if (opt.table_start_log2 < 0 || opt.table_start_log2 > 40) return bad(CC_ERR_INVALID, "table_start_log2 out of range");
+    if (opt.sweep_mode < 0 || opt.sweep_mode > 2) return bad(CC_ERR_INVALID, "sweep_mode must be 0, 1 or 2");
+    return CC_OK;
+}
+
+void finish_plan(Plan& p, const cc_options& opt)
+{
+    const int jobs = p.jobs;
+    p.persistent = 0;
+    p.temporary = 0;
+    p.hist_cap = jobs == 1 ? (1 << 16) : std::max(64, (int)opt.max_sweeps);
+    // a light sweep adds at most 2 x (the label rows its proposals move) keys,
+    // at most 1/4 of sum k n when sweeps choose between light and heavy, so
+    // 2 sum k n slots keep every sweep below the 7/8 fill limit; sweeps that
+    // are always light may move every row and need twice that
+    const unsigned long long want = (opt.sweep_mode == 1 ? 4ull : 2ull) * (unsigned long long)p.keys + 64;
+    p.cap_max = opt.table_log2 > 0 ? (1ull << opt.table_log2) : next_pow2(want);
+    if (p.cap_max < 64) p.cap_max = 64;
+    p.cap_start = opt.table_start_log2 > 0 ? (1ull << opt.table_start_log2) : next_pow2(2ull * p.keys + 64);
+    if (p.cap_start > p.cap_max) p.cap_start = p.cap_max;
+    p.lcap = next_pow2(2ull * p.keys + 64);
+    const size_t N = (size_t)p.n, J = (size_t)jobs;
+    const size_t per[] = {
+        sizeof(JobInfo) * J, sizeof(JobState) * J, 8 * (N + 1), 4 * (size_t)p.nnz, 4 * (size_t)p.nnz,
+        4 * N, 4 * (size_t)p.rows, 16 * (size_t)p.rows, 4 * N, 4 * N, 4 * N, 8 * N, 4 * N,
+        sizeof(Slot) * (size_t)p.cap_max, 4 * N, 4 * N, 4 * N, 4 * N, N, 4 * N, 4 * N, 4 * (N / 1024 + 2),
+        4 * (3 * N + N / 1024 + 64), sizeof(DevState), sizeof(cc_sweep_info) * J * (size_t)p.hist_cap};
+    for (size_t b : per) p.persistent += rounded(b);
+    const size_t tmp[] = {8 * (N + J), 8 * (J + 1), 4 * (size_t)p.keys, 8 * (J + 1), 4 * (size_t)p.parts, 4 * J,
+                          16 * (size_t)p.lcap};
+    for (size_t b : tmp) p.temporary += rounded(b);
+}
+
+}  // namespace ccg
+
+namespace {
+
+cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_options* opt_in, void* stream,
+                        cudaMemPool_t pool, cc_ctx** out)
 {
     if (!out) return fail(nullptr, CC_ERR_INVALID, "out is NULL");
     *out = nullptr;
-    if (n < 1) return fail(nullptr, CC_ERR_INVALID, "n must be >= 1");
-    if (k < 1) return fail(nullptr, CC_ERR_INVALID, "k must be >= 1");
-    if (k > 4096) return fail(nullptr, CC_ERR_INVALID, "k must be <= 4096");
-    if (nnz < 0) return fail(nullptr, CC_ERR_INVALID, "nnz must be >= 0");
-    if (!row_off || !labels || (nnz > 0 && !col)) return fail(nullptr, CC_ERR_INVALID, "null input pointer");
-    if (3LL * k * n + k >= (1LL << 31)) return fail(nullptr, CC_ERR_OVERFLOW, "3 k n + k >= 2^31");
-    if (opt) {
-        for (int r : opt->reserved)
-            if (r != 0) return fail(nullptr, CC_ERR_INVALID, "reserved option fields must be zero");
-        if (opt->table_log2 < 0 || opt->table_log2 > 40) return fail(nullptr, CC_ERR_INVALID, "table_log2 out of range");
-        if (opt->table_start_log2 < 0 || opt->table_start_log2 > 40)
-            return fail(nullptr, CC_ERR_INVALID, "table_start_log2 out of range");
-        if (opt->sweep_mode < 0 || opt->sweep_mode > 2) return fail(nullptr, CC_ERR_INVALID, "sweep_mode must be 0, 1 or 2");
-    }
+    const cc_options opt = resolve_options(opt_in);
+    Plan plan;
+    std::string msg;
+    cc_status pr = plan_jobs(jobs, in, opt, &plan, &msg);
+    if (pr != CC_OK) return fail(nullptr, pr, msg);
+    for (int j = 0; j < jobs; ++j)
+        if (!in[j].row_off || !in[j].labels || (in[j].nnz > 0 && !in[j].col))
+            return fail(nullptr, CC_ERR_INVALID, (jobs > 1 ? "job " + std::to_string(j) + ": " : std::string()) +
+                                                     "null input pointer");
+    const long long N = plan.n, NNZ = plan.nnz, rows = plan.rows, keys = plan.keys;
+    const int kmax = plan.kmax;
 
     cc_ctx* c = new cc_ctx();
-    c->n = n;
-    c->k = k;
-    c->kp = (k + 3) & ~3;
-    while ((1LL << c->lshift) < n) ++c->lshift;
-    c->nnz = nnz;
-    if (opt) c->opt = *opt;
-    else cc_default_options(&c->opt);
-    if (c->opt.max_sweeps <= 0) c->opt.max_sweeps = 20;
+    c->jobs = jobs;
+    c->kmax = kmax;
+    c->n = N;
+    c->nnz = NNZ;
+    c->rows = rows;
+    c->keys = keys;
+    c->opt = opt;
+    c->pool = pool;
+    c->hist_cap = plan.hist_cap;
 
     auto bail = [&](cc_status code) {
         g_create_error = c->err;
@@ -331,102 +424,200 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
     CC_TRY(cudaGetDevice(&c->device));
     CC_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     CC_TRY(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
-    c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+    // pooled memory is allocated in the order of the context's own stream, so
+    // such a context runs on that stream
+    c->stream = (stream && !pool) ? static_cast<cudaStream_t>(stream) : c->own_stream;
 
-    const unsigned long long kn = (unsigned long long)k * n;
-    unsigned long long cap = c->opt.table_log2 > 0 ? (1ull << c->opt.table_log2) : next_pow2(4 * kn + 64);
-    if (cap < 64) cap = 64;
+    // job table
+    c->job.resize(jobs);
+    std::vector<long long> eo(jobs + 1, 0), lo(jobs + 1, 0);
+    std::vector<int> pjob, pfirst(jobs);
+    long long vo = 0, go = 0;
+    for (int j = 0; j < jobs; ++j) {
+        JobInfo& J = c->job[j];
+        J.vo = vo;
+        J.n = in[j].n;
+        J.go = go;
+        J.k = in[j].k;
+        J.kp = (in[j].k + 3) & ~3;
+        J.lshift = 0;
+        while ((1LL << J.lshift) < J.n) ++J.lshift;
+        J.pad = 0;
+        vo += J.n;
+        go += J.n * J.kp;
+        eo[j + 1] = eo[j] + in[j].nnz;
+        lo[j + 1] = lo[j] + (long long)in[j].k * in[j].n;
+        pfirst[j] = (int)pjob.size();
+        for (int i = 0; i < in[j].k; ++i) pjob.push_back(j);
+    }
 
-    CC_TRY(dalloc(c, &c->off, (size_t)n + 1));
-    CC_TRY(dalloc(c, &c->col, (size_t)nnz));
-    CC_TRY(dalloc(c, &c->src, (size_t)nnz));
-    CC_TRY(dalloc(c, &c->aown, (size_t)n));
-    CC_TRY(dalloc(c, &c->G, (size_t)n * c->kp));
-    CC_TRY(dalloc(c, &c->C, (size_t)n));
-    CC_TRY(dalloc(c, &c->size, (size_t)n));
-    CC_TRY(dalloc(c, &c->dsize, (size_t)n));
-    CC_TRY(dalloc(c, &c->best, (size_t)n));
+    const unsigned long long cap = plan.cap_max;
+    c->cap_max = cap;
+
+    CC_TRY(dalloc(c, &c->d_job, (size_t)jobs));
+    CC_TRY(dalloc(c, &c->js, (size_t)jobs));
+    CC_TRY(dalloc(c, &c->off, (size_t)N + 1));
+    CC_TRY(dalloc(c, &c->col, (size_t)NNZ));
+    CC_TRY(dalloc(c, &c->src, (size_t)NNZ));
+    CC_TRY(dalloc(c, &c->jid, (size_t)N));
+    CC_TRY(dalloc(c, &c->G, (size_t)rows));
+    CC_TRY(dalloc(c, &c->summ, (size_t)rows));
+    CC_TRY(dalloc(c, &c->C, (size_t)N));
+    CC_TRY(dalloc(c, &c->size, (size_t)N));
+    CC_TRY(dalloc(c, &c->dsize, (size_t)N));
+    CC_TRY(dalloc(c, &c->best, (size_t)N));
+    CC_TRY(dalloc(c, &c->aown, (size_t)N));
     CC_TRY(dalloc(c, &c->table, (size_t)cap));
-    CC_TRY(dalloc(c, &c->pv, (size_t)n));
-    CC_TRY(dalloc(c, &c->pa, (size_t)n));
-    CC_TRY(dalloc(c, &c->pb, (size_t)n));
-    CC_TRY(dalloc(c, &c->pg, (size_t)n));
-    CC_TRY(dalloc(c, &c->pflag, (size_t)n));
-    CC_TRY(dalloc(c, &c->pslot, 2 * (size_t)kn));
-    CC_TRY(dalloc(c, &c->scratch, 3 * (size_t)n + (size_t)n / 1024 + 64));
-    CC_TRY(dalloc(c, &c->members, (size_t)n));
-    CC_TRY(dalloc(c, &c->summ, (size_t)n * c->kp));
-    CC_TRY(dalloc(c, &c->cursor, (size_t)n));
-    CC_TRY(dalloc(c, &c->bsum, (size_t)n / 1024 + 2));
+    CC_TRY(dalloc(c, &c->pv, (size_t)N));
+    CC_TRY(dalloc(c, &c->pa, (size_t)N));
+    CC_TRY(dalloc(c, &c->pb, (size_t)N));
+    CC_TRY(dalloc(c, &c->pg, (size_t)N));
+    CC_TRY(dalloc(c, &c->pflag, (size_t)N));
+    CC_TRY(dalloc(c, &c->members, (size_t)N));
+    CC_TRY(dalloc(c, &c->cursor, (size_t)N));
+    CC_TRY(dalloc(c, &c->bsum, (size_t)N / 1024 + 2));
+    CC_TRY(dalloc(c, &c->scratch, 3 * (size_t)N + (size_t)N / 1024 + 64));
     CC_TRY(dalloc(c, &c->st, 1));
-    CC_TRY(dalloc(c, &c->hist, (size_t)c->hist_cap));
-
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CC_TRY(cudaMemcpyAsync(c->off, row_off, sizeof(long long) * ((size_t)n + 1), kind, c->stream));
-    if (nnz > 0) CC_TRY(cudaMemcpyAsync(c->col, col, sizeof(int) * (size_t)nnz, kind, c->stream));
+    CC_TRY(dalloc(c, &c->hist, (size_t)jobs * c->hist_cap));
+    CC_TRY(cudaMemcpyAsync(c->d_job, c->job.data(), sizeof(JobInfo) * jobs, cudaMemcpyHostToDevice, c->stream));
 
     DevState s0;
     std::memset(&s0, 0, sizeof(s0));
     CC_TRY(cudaMemcpyAsync(c->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream));
-    CC_TRY(launch_validate(n, nnz, c->off, c->col, c->st, c->stream));
-    DevState s;
-    if (read_state(c, &s) != CC_OK) return bail(CC_ERR_CUDA);
-    if (s.err) return bail(fail(c, CC_ERR_INVALID, "malformed CSR: offsets must start at 0, end at nnz and not decrease; columns must lie in [0, n)"));
-    CC_TRY(launch_fill_src(n, c->off, c->src, c->stream));
+    std::vector<JobState> js0(jobs);
+    std::memset(js0.data(), 0, sizeof(JobState) * jobs);
+    CC_TRY(cudaMemcpyAsync(c->js, js0.data(), sizeof(JobState) * jobs, cudaMemcpyHostToDevice, c->stream));
 
-    // label compaction (scratch: the label map and, for host input, a device copy)
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // staging: offsets of every job whole (n + 1 each), labels partition-major per job
     {
-        int* dlabels = nullptr;
+        long long* offstage = nullptr;
+        long long* d_eo = nullptr;
+        int* labels = nullptr;
+        long long* d_lo = nullptr;
+        int* d_pjob = nullptr;
+        int* d_pfirst = nullptr;
         void* lmap = nullptr;
-        const unsigned long long lcap = next_pow2(2 * kn + 64);
-        cudaError_t e = cudaSuccess;
-        if (!on_device) {
-            e = cudaMalloc(&dlabels, sizeof(int) * kn);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(dlabels, labels, sizeof(int) * kn, cudaMemcpyHostToDevice, c->stream);
+        const unsigned long long lcap = plan.lcap;
+        std::vector<void*> temp;
+        auto tmalloc = [&](void** p, size_t bytes) {
+            bytes = bytes > 0 ? bytes : 16;
+            cudaError_t e = c->pool ? cudaMallocFromPoolAsync(p, bytes, c->pool, c->own_stream) : cudaMalloc(p, bytes);
+            if (e == cudaSuccess) temp.push_back(*p);
+            return e;
+        };
+        auto cleanup = [&]() {
+            if (c->pool) {
+                for (void* p : temp) cudaFreeAsync(p, c->own_stream);
+            } else {
+                cudaStreamSynchronize(c->stream);
+                for (void* p : temp) cudaFree(p);
+            }
+        };
+        cudaError_t e = tmalloc((void**)&offstage, sizeof(long long) * ((size_t)N + jobs));
+        if (e == cudaSuccess) e = tmalloc((void**)&d_eo, sizeof(long long) * (jobs + 1));
+        if (e == cudaSuccess) e = tmalloc((void**)&labels, sizeof(int) * (size_t)keys);
+        if (e == cudaSuccess) e = tmalloc((void**)&d_lo, sizeof(long long) * (jobs + 1));
+        if (e == cudaSuccess) e = tmalloc((void**)&d_pjob, sizeof(int) * pjob.size());
+        if (e == cudaSuccess) e = tmalloc((void**)&d_pfirst, sizeof(int) * jobs);
+        if (e == cudaSuccess) e = tmalloc(&lmap, 16 * lcap);
+        for (int j = 0; j < jobs && e == cudaSuccess; ++j) {
+            const JobInfo& J = c->job[j];
+            e = cudaMemcpyAsync(offstage + J.vo + j, in[j].row_off, sizeof(long long) * ((size_t)J.n + 1), kind, c->stream);
+            if (e == cudaSuccess && in[j].nnz > 0)
+                e = cudaMemcpyAsync(c->col + eo[j], in[j].col, sizeof(int) * (size_t)in[j].nnz, kind, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(labels + lo[j], in[j].labels, sizeof(int) * (size_t)(lo[j + 1] - lo[j]), kind, c->stream);
         }
-        if (e == cudaSuccess) e = cudaMalloc(&lmap, 16 * lcap);
-        if (e == cudaSuccess)
-            e = launch_compact_labels(n, k, c->kp, c->lshift, on_device ? labels : dlabels, c->G, lmap, lcap - 1, c->st,
-                                      c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_eo, eo.data(), sizeof(long long) * (jobs + 1), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_lo, lo.data(), sizeof(long long) * (jobs + 1), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_pjob, pjob.data(), sizeof(int) * pjob.size(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_pfirst, pfirst.data(), sizeof(int) * jobs, cudaMemcpyHostToDevice, c->stream);
+        AssemblyArgs as{};
+        as.jobs = jobs;
+        as.n = N;
+        as.nnz = NNZ;
+        as.offstage = offstage;
+        as.eo = d_eo;
+        as.job = c->d_job;
+        as.off = c->off;
+        as.col = c->col;
+        as.src = c->src;
+        as.jid = c->jid;
+        as.st = c->st;
+        if (e == cudaSuccess) e = launch_assemble(as, c->stream);
+        DevState s;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&s, c->st, sizeof(s), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (dlabels) cudaFree(dlabels);
-        if (lmap) cudaFree(lmap);
+        if (e != cudaSuccess) {
+            cleanup();
+            return bail(cuda_fail(c, e, "input assembly"));
+        }
+        if (s.err) {
+            cleanup();
+            return bail(fail(c, CC_ERR_INVALID, "malformed CSR: offsets must start at 0, end at nnz and not decrease; "
+                                                "columns must lie in [0, n)"));
+        }
+        e = launch_assemble_edges(as, c->stream);
+        LabelArgs la{};
+        la.jobs = jobs;
+        la.total = keys;
+        la.labels = labels;
+        la.lo = d_lo;
+        la.pjob = d_pjob;
+        la.pfirst = d_pfirst;
+        la.job = c->d_job;
+        la.js = c->js;
+        la.G = c->G;
+        la.lmap = lmap;
+        la.lmask = lcap - 1;
+        la.rows = rows;
+        la.st = c->st;
+        if (e == cudaSuccess) e = launch_compact_labels(la, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&s, c->st, sizeof(s), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cleanup();
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "label compaction"));
+        if (s.err) return bail(fail(c, CC_ERR_INVALID, "malformed CSR: columns must lie in [0, n)"));
     }
-    if (read_state(c, &s) != CC_OK) return bail(CC_ERR_CUDA);
-    if (s.err) return bail(fail(c, CC_ERR_INVALID, "label compaction failed"));
-    c->partition_sq = s.partition_sq;
-    c->F0 = c->partition_sq - (long long)k * n;
-    c->cap_start = c->opt.table_start_log2 > 0 ? (1ull << c->opt.table_start_log2) : next_pow2(2 * kn + 64);
-    if (c->cap_start > cap) c->cap_start = cap;
-    c->cap_max = cap;
+    std::vector<JobState> js;
+    if (read_jobs(c, js) != CC_OK) return bail(CC_ERR_CUDA);
+    c->F0.resize(jobs);
+    c->psq.resize(jobs);
+    for (int j = 0; j < jobs; ++j) {
+        c->psq[j] = js[j].partition_sq;
+        c->F0[j] = c->psq[j] - (long long)c->job[j].k * c->job[j].n;
+    }
+    c->cap_start = plan.cap_start;
 
     SweepArgs& a = c->args;
-    a.n = n;
-    a.k = k;
-    a.kp = c->kp;
-    a.nnz = nnz;
+    a.n = N;
+    a.nnz = NNZ;
+    a.jobs = jobs;
+    a.kmax = kmax;
     a.off = c->off;
     a.col = c->col;
     a.src = c->src;
-    a.aown = c->aown;
+    a.jid = c->jid;
+    a.job = c->d_job;
+    a.js = c->js;
     a.G = c->G;
+    a.summ = c->summ;
     a.C = c->C;
     a.size = c->size;
     a.dsize = c->dsize;
     a.best = c->best;
+    a.aown = c->aown;
     a.table = c->table;
-    a.summ = c->summ;
-    a.lshift = c->lshift;
-    a.sweep_mode = c->opt.sweep_mode;
     a.mask_max = cap - 1;
     a.cap_min = cap < 1024 ? cap : 1024;
+    a.keys = (unsigned long long)keys;
+    a.sweep_mode = c->opt.sweep_mode;
     a.pv = c->pv;
     a.pa = c->pa;
     a.pb = c->pb;
     a.pg = c->pg;
     a.pflag = c->pflag;
-    a.pslot = c->pslot;
     a.members = c->members;
     a.cursor = c->cursor;
     a.bsum = c->bsum;
@@ -435,8 +626,8 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
     a.hist_cap = c->hist_cap;
 
     int per_sm = 0;
-    CC_TRY(prepare_propose(c->kp, &per_sm));
-    if (per_sm < 1) return bail(fail(c, CC_ERR_INVALID, "proposal kernel cannot be resident for this k"));
+    CC_TRY(prepare_propose(&per_sm));
+    if (per_sm < 1) return bail(fail(c, CC_ERR_INVALID, "proposal kernel cannot be resident"));
     c->grid = c->sms * per_sm;
 
     cc_status rc = start_state(c);
@@ -446,22 +637,23 @@ cc_status create_common(int32_t n, int64_t nnz, const int64_t* row_off, const in
 #undef CC_TRY
 }
 
-// Output renumbering: first[c] = least vertex of cluster c; flag[first[c]] = 1;
-// rank = exclusive prefix sum of flags; label[v] = rank[first[C[v]]].
-__global__ void k_first(int n, int* first)
+// ---- output renumbering ----------------------------------------------------
+// first[c] = least vertex of cluster c; flag[v] = 1 iff v is first of its
+// cluster; rank = exclusive prefix sum of flags; label[v] = rank[first[C[v]]]
+// minus rank[first vertex of v's job] (labels count from 0 in each job).
+__global__ void k_first(long long n, int* first)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) first[v] = 0x7fffffff;
 }
 
-__global__ void k_first_min(int n, const int* __restrict__ C, int* first)
+__global__ void k_first_min(long long n, const int* __restrict__ C, int* first)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) atomicMin(&first[C[v]], (int)v);
 }
 
-// flag[v] = 1 iff v is the least vertex of its cluster; per-block counts.
-__global__ void k_flags(int n, const int* __restrict__ C, const int* __restrict__ first, int* flag, int* blocksum)
+__global__ void k_flags(long long n, const int* __restrict__ C, const int* __restrict__ first, int* flag, int* blocksum)
 {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
@@ -477,7 +669,7 @@ __global__ void k_flags(int n, const int* __restrict__ C, const int* __restrict_
 
 // Exclusive scan of the nb block counts by one block of 1024 threads, each
 // owning a contiguous run of counts.
-__global__ void k_scan_blocks(int nb, int* blocksum)
+__global__ void k_scan_counts(int nb, int* blocksum)
 {
     __shared__ int part[1024];
     const int per = (nb + 1023) / 1024;
@@ -501,7 +693,7 @@ __global__ void k_scan_blocks(int nb, int* blocksum)
 }
 
 // Within-block exclusive scan of the flags plus the block offset -> rank in place.
-__global__ void k_rank(int n, int* flag, const int* blocksum)
+__global__ void k_rank(long long n, int* flag, const int* blocksum)
 {
     __shared__ int buf[1024];
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -517,16 +709,166 @@ __global__ void k_rank(int n, int* flag, const int* blocksum)
     if (v < n) flag[v] = blocksum[blockIdx.x] + buf[threadIdx.x] - f;
 }
 
-__global__ void k_relabel(int n, const int* __restrict__ C, const int* __restrict__ first,
-                          const int* __restrict__ rank, int* out)
+__global__ void k_relabel(long long n, const int* __restrict__ C, const int* __restrict__ first,
+                          const int* __restrict__ rank, const int* __restrict__ jid, const JobInfo* __restrict__ job,
+                          int* out)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) out[v] = rank[first[C[v]]];
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        out[v] = rank[first[C[v]]] - rank[job[jid[v]].vo];
+}
+
+// Job-local cluster ids (C[v] - first vertex of v's job), or the reverse.
+__global__ void k_shift_ids(long long n, const int* __restrict__ in, const int* __restrict__ jid,
+                            const JobInfo* __restrict__ job, int sign, int* out)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        out[v] = (int)((unsigned)in[v] + (unsigned)sign * (unsigned)job[jid[v]].vo);
+}
+
+// Renumbered labels of every vertex into scratch + 2n (device); returns that pointer.
+cc_status renumber(cc_ctx* c, int** labels)
+{
+    const long long n = c->n;
+    int* first = c->scratch;
+    int* rank = c->scratch + n;
+    int* lab = c->scratch + 2 * (size_t)n;
+    int* blocksum = c->scratch + 3 * (size_t)n;
+    const int nb = (int)((n + 1023) / 1024);
+    const int g = c->sms * 8;
+    k_first<<<g, 256, 0, c->stream>>>(n, first);
+    k_first_min<<<g, 256, 0, c->stream>>>(n, c->C, first);
+    k_flags<<<nb, 1024, 0, c->stream>>>(n, c->C, first, rank, blocksum);
+    k_scan_counts<<<1, 1024, 0, c->stream>>>(nb, blocksum);
+    k_rank<<<nb, 1024, 0, c->stream>>>(n, rank, blocksum);
+    k_relabel<<<g, 256, 0, c->stream>>>(n, c->C, first, rank, c->jid, c->d_job, lab);
+    c->launches += 6;
+    CC_CUDA(c, cudaGetLastError());
+    *labels = lab;
+    return CC_OK;
+}
+
+cc_status check_job(cc_ctx* c, int32_t job)
+{
+    if (!c) return fail(nullptr, CC_ERR_INVALID, "ctx is NULL");
+    if (job < 0 || job >= c->jobs) return fail(c, CC_ERR_INVALID, "job index out of range");
+    return CC_OK;
+}
+
+cc_status launch_chunk(cc_ctx* c)
+{
+    const int chunk = c->async_limit < kChunk ? c->async_limit : kChunk;
+    RunGraph* g = nullptr;
+    cc_status r = ensure_graph(c, chunk, &g);
+    if (r != CC_OK) return r;
+    CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
+    c->launches += (long long)chunk * kKernelsPerSweep;
+    CC_CUDA(c, cudaMemcpyAsync(c->hstate, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaEventRecord(c->chunk_done, c->stream));
+    c->async_launches += 1;
+    return CC_OK;
 }
 
 }  // namespace
 
+namespace ccg {
+
+cc_status ctx_create(int jobs, const JobInput* in, bool on_device, const cc_options* opt, void* stream,
+                     cudaMemPool_t pool, cc_ctx** out)
+{
+    return create_common(jobs, in, on_device, opt, stream, pool, out);
+}
+
+cc_status ctx_async_start(cc_ctx* c, int limit, DevState* pinned)
+{
+    c->hstate = pinned;
+    c->async_limit = limit > 0 ? limit : c->opt.max_sweeps;
+    c->async_launches = 0;
+    if (!c->chunk_done) CC_CUDA(c, cudaEventCreateWithFlags(&c->chunk_done, cudaEventDisableTiming));
+    CC_CUDA(c, launch_run_begin(c->args, c->async_limit, c->stream));
+    c->launches += 1;
+    return launch_chunk(c);
+}
+
+int ctx_async_poll(cc_ctx* c, cc_status* st)
+{
+    *st = CC_OK;
+    const cudaError_t q = cudaEventQuery(c->chunk_done);
+    if (q == cudaErrorNotReady) return 0;
+    if (q != cudaSuccess) {
+        *st = cuda_fail(c, q, "sweep chunk");
+        return -1;
+    }
+    const DevState s = *c->hstate;
+    if (s.err) {
+        *st = check_device_error(c, s);
+        return -1;
+    }
+    if (s.stop) return 1;
+    // each launch runs up to 4 sweep bodies; abandoned sweeps are retried
+    if (c->async_launches > c->async_limit + 64) {
+        *st = fail(c, CC_ERR_TABLE_FULL, "sweep retries did not converge");
+        return -1;
+    }
+    *st = launch_chunk(c);
+    return *st == CC_OK ? 0 : -1;
+}
+
+cc_status ctx_job_results(cc_ctx* c, std::vector<long long>& F, std::vector<int>& sweeps)
+{
+    std::vector<JobState> js;
+    cc_status r = read_jobs(c, js);
+    if (r != CC_OK) return r;
+    F.resize(c->jobs);
+    sweeps.resize(c->jobs);
+    for (int j = 0; j < c->jobs; ++j) {
+        F[j] = js[j].F;
+        sweeps[j] = js[j].sweeps;
+    }
+    return CC_OK;
+}
+
+cc_status ctx_renumber(cc_ctx* c, int** dev_labels)
+{
+    return renumber(c, dev_labels);
+}
+
+cc_status ctx_copy_labels(cc_ctx* c, const int* dev_labels, int j, int32_t* out)
+{
+    const JobInfo& J = c->job[j];
+    CC_CUDA(c, cudaMemcpyAsync(out, dev_labels + J.vo, sizeof(int) * (size_t)J.n, cudaMemcpyDeviceToHost, c->stream));
+    return CC_OK;
+}
+
+void ctx_destroy(cc_ctx* c)
+{
+    if (!c) return;
+    if (!c->pool && c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+}  // namespace ccg
+
 extern "C" {
+
+cc_status cc_estimate_bytes(int32_t jobs, const cc_job_desc* descs, const cc_options* opt, int64_t* persistent,
+                            int64_t* peak)
+{
+    if (jobs < 1 || !descs) return fail(nullptr, CC_ERR_INVALID, "cc_estimate_bytes needs jobs >= 1 and descriptors");
+    std::vector<JobInput> in(jobs);
+    for (int j = 0; j < jobs; ++j)
+        in[j] = JobInput{descs[j].n, descs[j].nnz, descs[j].row_off, descs[j].col, descs[j].k, descs[j].labels};
+    Plan p;
+    std::string msg;
+    cc_status r = plan_jobs(jobs, in.data(), resolve_options(opt), &p, &msg);
+    if (r != CC_OK) return fail(nullptr, r, msg);
+    if (persistent) *persistent = (int64_t)p.persistent;
+    if (peak) *peak = (int64_t)(p.persistent + p.temporary);
+    return CC_OK;
+}
+
 
 void cc_default_options(cc_options* opt)
 {
@@ -538,13 +880,27 @@ void cc_default_options(cc_options* opt)
 cc_status cc_create(int32_t n, int64_t nnz, const int64_t* row_off, const int32_t* col, int32_t k,
                     const int32_t* labels, const cc_options* opt, cc_ctx** out)
 {
-    return create_common(n, nnz, row_off, col, k, labels, false, opt, nullptr, out);
+    const JobInput in{n, nnz, row_off, col, k, labels};
+    return create_common(1, &in, false, opt, nullptr, nullptr, out);
 }
 
 cc_status cc_create_dev(int32_t n, int64_t nnz, const int64_t* row_off_dev, const int32_t* col_dev, int32_t k,
                         const int32_t* labels_dev, const cc_options* opt, void* stream, cc_ctx** out)
 {
-    return create_common(n, nnz, row_off_dev, col_dev, k, labels_dev, true, opt, stream, out);
+    const JobInput in{n, nnz, row_off_dev, col_dev, k, labels_dev};
+    return create_common(1, &in, true, opt, stream, nullptr, out);
+}
+
+cc_status cc_batch_create(int32_t jobs, const cc_job_desc* descs, const cc_options* opt, cc_ctx** out)
+{
+    if (jobs < 1 || !descs) {
+        if (out) *out = nullptr;
+        return fail(nullptr, CC_ERR_INVALID, "cc_batch_create needs jobs >= 1 and descriptors");
+    }
+    std::vector<JobInput> in(jobs);
+    for (int j = 0; j < jobs; ++j)
+        in[j] = JobInput{descs[j].n, descs[j].nnz, descs[j].row_off, descs[j].col, descs[j].k, descs[j].labels};
+    return create_common(jobs, in.data(), false, opt, nullptr, nullptr, out);
 }
 
 cc_status cc_set_stream(cc_ctx* c, void* stream)
@@ -564,43 +920,70 @@ cc_status cc_reset(cc_ctx* c)
 cc_status cc_set_cluster_ids(cc_ctx* c, const int32_t* C)
 {
     if (!c || !C) return fail(c, CC_ERR_INVALID, "null argument");
-    CC_CUDA(c, cudaMemcpyAsync(c->scratch, C, sizeof(int) * (size_t)c->n, cudaMemcpyHostToDevice, c->stream));
+    const long long n = c->n;
+    // job-local ids -> union ids in scratch[n .. 2n), checked before C is touched
+    CC_CUDA(c, cudaMemcpyAsync(c->scratch, C, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    k_shift_ids<<<c->sms * 8, 256, 0, c->stream>>>(n, c->scratch, c->jid, c->d_job, 1, c->scratch + n);
     DevState s;
     cc_status r = read_state(c, &s);
     if (r != CC_OK) return r;
-    // ids are checked before the context's own state is touched
     CC_CUDA(c, cudaMemsetAsync(&c->st->err, 0, sizeof(int), c->stream));
     SweepArgs probe = c->args;
-    probe.C = c->scratch;
-    probe.size = c->scratch + c->n;
-    probe.dsize = c->scratch + 2 * (size_t)c->n;
+    probe.C = c->scratch + n;
+    probe.size = c->scratch;  // the job-local copy is no longer needed
+    probe.dsize = c->scratch + 2 * (size_t)n;
+    probe.best = c->best;
     CC_CUDA(c, launch_state_from_ids(probe, c->stream));
-    c->launches += 2;
+    c->launches += 3;
     DevState chk;
     r = read_state(c, &chk);
     if (r != CC_OK) return r;
     if (chk.err) {
         CC_CUDA(c, cudaMemcpyAsync(&c->st->err, &s.err, sizeof(int), cudaMemcpyHostToDevice, c->stream));
         CC_CUDA(c, cudaStreamSynchronize(c->stream));
-        return fail(c, CC_ERR_INVALID, "cluster ids must lie in [0, n)");
+        return fail(c, CC_ERR_INVALID, "cluster ids must lie in [0, n) of their job");
     }
-    CC_CUDA(c, cudaMemcpyAsync(c->C, c->scratch, sizeof(int) * (size_t)c->n, cudaMemcpyDeviceToDevice, c->stream));
+    CC_CUDA(c, cudaMemcpyAsync(c->C, c->scratch + n, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
     const unsigned long long nm = c->cap_start - 1;
     CC_CUDA(c, cudaMemcpyAsync(&c->st->new_mask, &nm, sizeof(nm), cudaMemcpyHostToDevice, c->stream));
     CC_CUDA(c, launch_state_from_ids(c->args, c->stream));
-    CC_CUDA(c, launch_table_rebuild(c->args, false, c->stream));
+    CC_CUDA(c, launch_table_rebuild(c->args, c->rows, false, c->stream));
     c->launches += 2 + kKernelsPerRebuild;
-    long long F = 0;
-    r = objective_recompute(c, &F);
+    std::vector<long long> F;
+    r = objective_recompute(c, F);
     if (r != CC_OK) return r;
-    CC_CUDA(c, cudaMemcpyAsync(&c->st->F, &F, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+    std::vector<JobState> js;
+    r = read_jobs(c, js);
+    if (r != CC_OK) return r;
+    for (int j = 0; j < c->jobs; ++j) {
+        js[j].F = F[j];
+        js[j].stop = 1;
+    }
+    CC_CUDA(c, cudaMemcpyAsync(c->js, js.data(), sizeof(JobState) * c->jobs, cudaMemcpyHostToDevice, c->stream));
     int one = 1;
     CC_CUDA(c, cudaMemcpyAsync(&c->st->stop, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    CC_CUDA(c, cudaStreamSynchronize(c->stream));
     DevState after;
     r = read_state(c, &after);
     if (r != CC_OK) return r;
     return check_device_error(c, after);
+}
+
+cc_status cc_job_history(cc_ctx* c, int32_t job, int32_t max, cc_sweep_info* out, int32_t* count)
+{
+    cc_status r = check_job(c, job);
+    if (r != CC_OK) return r;
+    std::vector<JobState> js;
+    r = read_jobs(c, js);
+    if (r != CC_OK) return r;
+    const int have = std::min(js[job].sweeps, c->hist_cap);
+    if (count) *count = js[job].sweeps;
+    const int m = std::min(max, have);
+    if (m > 0 && out) {
+        CC_CUDA(c, cudaMemcpyAsync(out, c->hist + (size_t)job * c->hist_cap, sizeof(cc_sweep_info) * (size_t)m,
+                                   cudaMemcpyDeviceToHost, c->stream));
+        CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return CC_OK;
 }
 
 cc_status cc_sweep(cc_ctx* c, cc_sweep_info* info)
@@ -609,15 +992,18 @@ cc_status cc_sweep(cc_ctx* c, cc_sweep_info* info)
     cc_status r = run(c, 1, nullptr);
     if (r != CC_OK) return r;
     if (info) {
-        DevState s;
-        r = read_state(c, &s);
+        r = need_single(c);
         if (r != CC_OK) return r;
-        if (s.sweeps >= 1 && s.sweeps <= c->hist_cap) {
-            CC_CUDA(c, cudaMemcpyAsync(info, c->hist + (s.sweeps - 1), sizeof(cc_sweep_info), cudaMemcpyDeviceToHost, c->stream));
+        std::vector<JobState> js;
+        r = read_jobs(c, js);
+        if (r != CC_OK) return r;
+        const int s = js[0].sweeps;
+        if (s >= 1 && s <= c->hist_cap) {
+            CC_CUDA(c, cudaMemcpyAsync(info, c->hist + (s - 1), sizeof(cc_sweep_info), cudaMemcpyDeviceToHost, c->stream));
             CC_CUDA(c, cudaStreamSynchronize(c->stream));
         } else {
             std::memset(info, 0, sizeof(*info));
-            info->F = s.F;
+            info->F = js[0].F;
         }
     }
     return CC_OK;
@@ -670,42 +1056,52 @@ cc_status cc_launch_count(const cc_ctx* c, int64_t* out)
 cc_status cc_history(cc_ctx* c, int32_t max, cc_sweep_info* out, int32_t* count)
 {
     if (!c) return fail(nullptr, CC_ERR_INVALID, "ctx is NULL");
-    DevState s;
-    cc_status r = read_state(c, &s);
+    cc_status r = need_single(c);
     if (r != CC_OK) return r;
-    int have = s.sweeps < c->hist_cap ? s.sweeps : c->hist_cap;
-    if (count) *count = s.sweeps;
-    int m = max < have ? max : have;
-    if (m > 0 && out) {
-        CC_CUDA(c, cudaMemcpyAsync(out, c->hist, sizeof(cc_sweep_info) * (size_t)m, cudaMemcpyDeviceToHost, c->stream));
-        CC_CUDA(c, cudaStreamSynchronize(c->stream));
-    }
+    return cc_job_history(c, 0, max, out, count);
+}
+
+cc_status cc_job_objective(cc_ctx* c, int32_t job, int64_t* out, int32_t* sweeps)
+{
+    cc_status r = check_job(c, job);
+    if (r != CC_OK) return r;
+    std::vector<JobState> js;
+    r = read_jobs(c, js);
+    if (r != CC_OK) return r;
+    if (out) *out = js[job].F;
+    if (sweeps) *sweeps = js[job].sweeps;
     return CC_OK;
 }
 
 cc_status cc_objective(cc_ctx* c, int64_t* out)
 {
     if (!c || !out) return fail(c, CC_ERR_INVALID, "null argument");
-    DevState s;
-    cc_status r = read_state(c, &s);
+    cc_status r = need_single(c);
     if (r != CC_OK) return r;
-    *out = s.F;
-    return CC_OK;
+    return cc_job_objective(c, 0, out, nullptr);
 }
 
 cc_status cc_objective_recompute(cc_ctx* c, int64_t* out)
 {
     if (!c || !out) return fail(c, CC_ERR_INVALID, "null argument");
-    long long F = 0;
-    cc_status r = objective_recompute(c, &F);
-    if (r == CC_OK) *out = F;
+    cc_status r = need_single(c);
+    if (r != CC_OK) return r;
+    std::vector<long long> F;
+    r = objective_recompute(c, F);
+    if (r == CC_OK) *out = F[0];
     return r;
 }
 
 cc_status cc_cluster_ids(cc_ctx* c, int32_t* out)
 {
     if (!c || !out) return fail(c, CC_ERR_INVALID, "null argument");
-    CC_CUDA(c, cudaMemcpyAsync(out, c->C, sizeof(int) * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
+    const int* src = c->C;
+    if (c->jobs > 1) {
+        k_shift_ids<<<c->sms * 8, 256, 0, c->stream>>>(c->n, c->C, c->jid, c->d_job, -1, c->scratch);
+        c->launches += 1;
+        src = c->scratch;
+    }
+    CC_CUDA(c, cudaMemcpyAsync(out, src, sizeof(int) * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
     return CC_OK;
 }
@@ -720,23 +1116,32 @@ cc_status cc_cluster_ids_dev(cc_ctx* c, const int32_t** out)
 cc_status cc_consensus_labels(cc_ctx* c, int32_t* out)
 {
     if (!c || !out) return fail(c, CC_ERR_INVALID, "null argument");
-    const int n = c->n;
-    int* first = c->scratch;
-    int* rank = c->scratch + n;
-    int* lab = c->scratch + 2 * (size_t)n;
-    int* blocksum = c->scratch + 3 * (size_t)n;
-    const int nb = (n + 1023) / 1024;
-    const int g = c->sms * 8;
-    k_first<<<g, 256, 0, c->stream>>>(n, first);
-    k_first_min<<<g, 256, 0, c->stream>>>(n, c->C, first);
-    k_flags<<<nb, 1024, 0, c->stream>>>(n, c->C, first, rank, blocksum);
-    k_scan_blocks<<<1, 1024, 0, c->stream>>>(nb, blocksum);
-    k_rank<<<nb, 1024, 0, c->stream>>>(n, rank, blocksum);
-    k_relabel<<<g, 256, 0, c->stream>>>(n, c->C, first, rank, lab);
-    c->launches += 6;
-    CC_CUDA(c, cudaGetLastError());
-    CC_CUDA(c, cudaMemcpyAsync(out, lab, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    int* lab = nullptr;
+    cc_status r = renumber(c, &lab);
+    if (r != CC_OK) return r;
+    CC_CUDA(c, cudaMemcpyAsync(out, lab, sizeof(int) * (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CC_OK;
+}
+
+cc_status cc_job_labels(cc_ctx* c, int32_t job, int32_t* out)
+{
+    cc_status r = check_job(c, job);
+    if (r != CC_OK) return r;
+    if (!out) return fail(c, CC_ERR_INVALID, "null argument");
+    int* lab = nullptr;
+    r = renumber(c, &lab);
+    if (r != CC_OK) return r;
+    const JobInfo& J = c->job[job];
+    CC_CUDA(c, cudaMemcpyAsync(out, lab + J.vo, sizeof(int) * (size_t)J.n, cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CC_OK;
+}
+
+cc_status cc_job_count(const cc_ctx* c, int32_t* out)
+{
+    if (!c || !out) return fail(nullptr, CC_ERR_INVALID, "null argument");
+    *out = c->jobs;
     return CC_OK;
 }
 
@@ -747,10 +1152,7 @@ const char* cc_last_error(const cc_ctx* c)
 
 void cc_destroy(cc_ctx* c)
 {
-    if (!c) return;
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    free_all(c);
-    delete c;
+    ctx_destroy(c);
 }
 
 }  // extern "C"

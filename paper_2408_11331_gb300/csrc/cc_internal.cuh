@@ -1,25 +1,33 @@
 // Internal declarations shared by the CUDA translation units of libcc.so.
 //
-// Device data layout (one consensus job):
-//   off   int64[n+1]   CSR row offsets            col  int32[nnz]  neighbours
-//   G     int32[n][kp] compacted label ids, vertex-major, kp = k rounded up to 4 so
-//                      that each row is 16-byte aligned; g = (i << s) | rep where rep
-//                      is the least vertex carrying that label in partition i and
-//                      2^s >= n, so g identifies (partition, label), i = g >> s and
-//                      g < k 2^s < 2 k n.  Padding = -1.
-//   summ  int4[n][kp]  per (cluster x, partition i): {d, m, m2, 0} with d the label id
-//                      that was most frequent in x at the last table rebuild, m the
-//                      exact current count of d in x (kept by every commit) and m2 an
-//                      upper bound on the count of every other label of partition i
-//                      in x (raised by commits, recomputed at rebuilds).
-//   C     int32[n]     cluster id of each vertex (founding-vertex ids)
-//   size  int32[n]     cluster sizes, indexed by cluster id
-//   table Slot[cap]    the contingency counts n(c, i, l) as an open-addressing
-//                      hash with linear probing, key = c << 32 | g.  The buffer holds
-//                      2^p >= 3 k n slots; only an active prefix of 2^q slots is used
-//                      (st->mask = 2^q - 1), grown before a sweep stages its moves and
-//                      shrunk when few keys are live, so that the probes of late
-//                      sweeps stay in L2.
+// A context holds J independent consensus jobs as one disjoint union (a
+// single job is J = 1).  Vertices of job j are the union ids vo_j .. vo_j+n_j-1;
+// cluster ids are union vertex ids (the founding vertex), so they never clash
+// across jobs and a cluster id also names its job.  Every step of a sweep runs
+// over the whole union in the same kernels; each job keeps its own counters,
+// guard decisions, objective, convergence and history, so a job's run is
+// identical to running it alone.
+//
+// Device data layout:
+//   off   int64[N+1]   union CSR row offsets      col  int32[NNZ] union neighbour ids
+//   src   int32[NNZ]   source vertex of each CSR entry
+//   jid   int32[N]     job of each vertex (and of each cluster id)
+//   G     int32[...]   compacted label ids, vertex-major: job j's rows start at go_j,
+//                      kp_j = k_j rounded up to 4 ints each (16-byte rows, padding -1);
+//                      g = (i << s_j) | rep, rep the job-local index of the least vertex
+//                      carrying that label in partition i and 2^s_j >= n_j, so g names
+//                      (partition, label) within the job and g < 2 k_j n_j.
+//   summ  int4[...]    same layout as G, one row per cluster id: per partition i
+//                      {d, m, m2, 0}: d the label id that was most frequent in the
+//                      cluster at the last table rebuild, m the exact current count of
+//                      d (kept by every commit), m2 an upper bound on the count of any
+//                      other label of partition i in the cluster.
+//   C     int32[N]     cluster id of each vertex
+//   size  int32[N]     cluster sizes, indexed by cluster id
+//   table Slot[cap]    the contingency counts n(c, i, l) of all jobs as one open-
+//                      addressing hash with linear probing, key = c << 32 | g.  Only an
+//                      active prefix of st->mask + 1 slots is used; it is rebuilt from C
+//                      (with dead keys dropped) when needed.
 #pragma once
 
 #include <cstdint>
@@ -33,7 +41,6 @@ namespace ccg {
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr int kWarpsPerBlock = 8;
 constexpr int kBlock = kWarpsPerBlock * 32;
-constexpr int kTile = 256;  // vertices claimed at once by a block of the proposal kernel
 
 // One contingency entry: the (cluster, label id) key, its count and the
 // delta staged by the current sweep.  16 bytes, read as one vector load.
@@ -43,70 +50,102 @@ struct __align__(16) Slot {
     int dlt;
 };
 
-// Device-resident control block of a context.
+// Static description of a job inside the union.
+struct JobInfo {
+    long long vo;   // first union vertex
+    long long n;    // vertices
+    long long go;   // first entry of the job's rows in G and summ
+    int k;          // input partitions
+    int kp;         // k rounded up to 4
+    int lshift;     // s_j
+    int pad;
+};
+
+// Per-job state of the current run.
+struct JobState {
+    unsigned long long nprop;  // |P| of the current sweep
+    unsigned long long np1;    // |P1|
+    unsigned long long moves;  // moves committed in the current sweep
+    long long dF;              // objective change of the current sweep
+    long long dF_p1;           // dF of P1 as evaluated
+    long long F;               // current objective
+    long long recompute;       // F' accumulator (heavy sweeps, recompute)
+    long long partition_sq;    // sum_i sum_j |P_ij|^2
+    int mode;                  // 0 nothing to commit, 1 commit P1 (staged), 2 matching, 3 P1 committed (rebuilt)
+    int stop;                  // 1: this job's run has stopped
+    int sweeps;                // sweeps recorded since creation / reset
+    int run_sweeps;            // sweeps in the current run
+    int rollback;              // 1: this heavy sweep's P1 was rejected and is being undone
+    int pad;
+};
+
+// Device-resident control block of a context (union-wide state).
 struct DevState {
-    unsigned long long nprop;    // |P| of the current sweep
-    unsigned long long np1;      // |P1|
-    long long dF;                // staged objective change
-    long long dF_p1;             // dF of P1 as evaluated
-    long long F;                 // current objective
-    unsigned long long moves;    // moves committed in the current sweep
+    unsigned long long nprop;    // proposals of the current sweep, all jobs
+    unsigned long long pkeys;    // sum over those proposals of their job's k (label rows they move)
     unsigned long long used;     // occupied table slots
     long long live;              // keys with a non-zero count
-    unsigned long long tile_ctr; // next vertex tile of the proposal kernel
     unsigned long long mask;     // active table capacity - 1 (a power of two minus one)
     unsigned long long new_mask; // capacity - 1 of a pending rebuild
-    long long partition_sq;      // sum_i sum_j |P_ij|^2
-    long long recompute;         // output of the full objective reduction
-    int mode;                    // 0 nothing to commit, 1 commit P1, 2 matching
+    unsigned long long tile_ctr; // work counter of the proposal step
+    int skip;                    // 1: this sweep does nothing (every job has stopped)
+    int stop;                    // 1: the run has stopped (all jobs)
+    int active;                  // jobs still running after the current sweep
+    int rebuild;                 // 1: a table rebuild is pending
+    int err;                     // cc_status of a device-side failure (first one wins)
     int overflow;                // 1: the table ran short during this sweep (nothing committed)
     int abort;                   // 1: the pending rebuild follows an abandoned sweep
     int retries;                 // sweeps abandoned and retried in a larger table
-    int heavy;                   // 1: this sweep evaluates P1 by a rebuild (see sweep.cu)
-    int rollback;                // 1: the heavy sweep's P1 was rejected and is being undone
-    int tvalid;                  // 1: the table holds the counts of the current C
     int rebuilds;                // table rebuilds since creation
-    int skip;                    // 1: this sweep does nothing (the run has stopped)
-    int stop;                    // 1: the run has stopped
-    int rebuild;                 // 1: a table rebuild is pending
-    int err;                     // cc_status of a device-side failure (first one wins)
-    int sweeps;                  // sweeps recorded since creation / reset
-    int run_sweeps;              // sweeps in the current run
+    int heavy;                   // 1: this sweep evaluates P1 by a rebuild (see sweep.cu)
+    int rollback;                // 1: some job's heavy P1 is being undone
+    int tvalid;                  // 1: the table holds the counts of the current C
     int run_limit;               // sweep limit of the current run
+    int run_bodies;              // sweeps of the current run that did work (retried ones included)
 };
 
-// Arguments of the sweep kernels (passed by value).
+// Arguments of the kernels (passed by value).
 struct SweepArgs {
-    int n, k, kp;
-    long long nnz;
+    long long n;                // N, union vertices
+    long long nnz;              // union CSR entries
+    int jobs;                   // J
+    int kmax;                   // largest k_j
     const long long* off;
     const int* col;
     const int* src;             // source vertex of each CSR entry (nnz)
+    const int* jid;             // job of each vertex
+    const JobInfo* job;         // J
+    JobState* js;               // J
     const int* G;
+    int4* summ;
     int* C;
     int* size;
     int* dsize;                 // staged size deltas
     unsigned long long* best;   // bids: per vertex in the proposal step, per cluster in the matching
     int* aown;                  // A_a of each vertex for the current sweep
     Slot* table;
-    int4* summ;                  // per-cluster label summaries (see above)
-    int lshift;                  // s: label id g = (i << s) | rep
-    int sweep_mode;              // 0 automatic, 1 always staged deltas, 2 always rebuild
     unsigned long long mask_max; // allocated capacity - 1; the active capacity is st->mask + 1
     unsigned long long cap_min;  // smallest active capacity
+    unsigned long long keys;     // sum_j k_j n_j: no C has more live keys
+    int sweep_mode;              // 0 automatic, 1 always staged deltas, 2 always rebuild
     int* pv;                    // proposal list: vertex,
     int* pa;                    //   source cluster,
     int* pb;                    //   target cluster,
     int* pg;                    //   gain dD
-    unsigned char* pflag;       //   1 if kept by the singleton guard
-    unsigned int* pslot;        //   table slots of (a, g_i(v)) and (b, g_i(v)), 2 per (j, i)
+    unsigned char* pflag;       //   1 if kept by the singleton guard (2: matching winner)
     int* members;               // rebuild scratch: vertices listed cluster by cluster (n)
     int* cursor;                // rebuild scratch: next free position of each cluster (n)
     int* bsum;                  // rebuild scratch: per-block sums of the size scan (n / 1024 + 1)
     DevState* st;
-    cc_sweep_info* hist;
+    cc_sweep_info* hist;        // J x hist_cap records
     int hist_cap;
 };
+
+// Row of vertex / cluster x (a union vertex id) of job J in G or summ.
+__device__ __forceinline__ long long row_of(const JobInfo& J, long long x)
+{
+    return J.go + (x - J.vo) * J.kp;
+}
 
 // 64-bit finaliser of MurmurHash3 (Austin Appleby, public domain); used by the
 // setup-time label map.
@@ -122,7 +161,7 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 
 // Slot hash of a (cluster, label id) key: the two 32-bit halves mixed with odd
 // multipliers, then the 32-bit MurmurHash3 finaliser.  Capacities stay below
-// 2^32 slots (at most 4 k n rounded up, with 3 k n < 2^31).
+// 2^32 slots.
 __device__ __forceinline__ unsigned long long hash_key(unsigned long long key)
 {
     unsigned h = ((unsigned)(key >> 32) * 0x9E3779B1u) ^ ((unsigned)key * 0x85EBCA77u);
@@ -142,10 +181,11 @@ __device__ __forceinline__ unsigned long long ckey(int c, int g)
 // Keeps the summary row of the slot's (cluster, partition) valid after its
 // count changed by d to newc: the count of the row's label is exact, the
 // bound on the other labels only rises.
-__device__ __forceinline__ void summ_update(int4* summ, int kp, int lshift, unsigned long long key, int d, int newc)
+__device__ __forceinline__ void summ_update(const SweepArgs& a, unsigned long long key, int d, int newc)
 {
     const int x = (int)(key >> 32), g = (int)(unsigned)(key & 0xffffffffull);
-    int4* S = summ + (long long)x * kp + (g >> lshift);
+    const JobInfo& J = a.job[a.jid[x]];
+    int4* S = a.summ + row_of(J, x) + (g >> J.lshift);
     if (S->x == g) atomicAdd(&S->y, d);
     else if (d > 0) atomicMax(&S->z, newc);
 }
@@ -154,6 +194,98 @@ __device__ __forceinline__ void set_err(DevState* st, int code)
 {
     atomicCAS(&st->err, 0, code);
 }
+
+// Adds x to the 64-bit field of job `job` in an array of JobState (field at
+// base, records stride_ll long longs apart): one atomic per warp when all of
+// its lanes belong to one job (the usual case), one per lane otherwise.
+// Every lane of the warp must call it; job < 0 adds nothing.
+__device__ __forceinline__ void job_add64(long long x, int job, long long* base, size_t stride_ll)
+{
+    const unsigned same = __match_any_sync(0xffffffffu, job);
+    if (same == 0xffffffffu) {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x != 0 && job >= 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(base + (size_t)job * stride_ll), (unsigned long long)x);
+    } else if (x != 0 && job >= 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(base + (size_t)job * stride_ll), (unsigned long long)x);
+    }
+}
+
+constexpr size_t kJobStride = sizeof(JobState) / sizeof(long long);
+
+// Per-job 64-bit sums over a kernel's loop: each thread keeps a running
+// (job, sum) and flushes it when its job changes -- into a shared-memory
+// array of per-job sums when the context has few jobs (sh != nullptr), else
+// straight into the job records -- and finish() adds what is left, once per
+// warp for one job.  For a single job that is one global atomic per warp per
+// launch instead of one per loop iteration.
+constexpr int kSmemJobs = 1024;
+
+struct JobAcc {
+    int job = -1;
+    long long sum = 0;
+    long long* sh;      // shared per-job sums or nullptr
+    long long* base;    // field of job 0 in the JobState array
+    size_t stride;
+
+    __device__ __forceinline__ JobAcc(long long* sh_, long long* base_, size_t stride_)
+        : sh(sh_), base(base_), stride(stride_) {}
+
+    __device__ __forceinline__ void flush()
+    {
+        if (job >= 0 && sum != 0) {
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(sh ? sh + job : base + (size_t)job * stride);
+            atomicAdd(dst, (unsigned long long)sum);
+        }
+        sum = 0;
+    }
+
+    __device__ __forceinline__ void add(int j, long long x)
+    {
+        if (x == 0) return;
+        if (j != job) {
+            flush();
+            job = j;
+        }
+        sum += x;
+    }
+};
+
+// Shared per-job sums of a block for contexts of 2..kSmemJobs jobs (dynamic
+// shared memory of smem_jobs_bytes(jobs)); nullptr otherwise.  Every thread
+// of the block must call it.
+__device__ __forceinline__ long long* job_smem_init(int jobs, long long* dyn)
+{
+    if (jobs < 2 || jobs > kSmemJobs) return nullptr;
+    for (int j = threadIdx.x; j < jobs; j += blockDim.x) dyn[j] = 0;
+    __syncthreads();
+    return dyn;
+}
+
+inline size_t smem_jobs_bytes(int jobs)
+{
+    return (jobs >= 2 && jobs <= kSmemJobs) ? sizeof(long long) * (size_t)jobs : 0;
+}
+
+// Adds what the accumulators of the block hold to the job records.  Every
+// thread of the block must call it, after its last add().
+__device__ __forceinline__ void job_acc_finish(JobAcc& acc, int jobs)
+{
+    if (acc.sh) {
+        acc.flush();
+        __syncthreads();
+        for (int j = threadIdx.x; j < jobs; j += blockDim.x) {
+            const long long x = acc.sh[j];
+            if (x != 0) atomicAdd(reinterpret_cast<unsigned long long*>(acc.base + (size_t)j * acc.stride),
+                                  (unsigned long long)x);
+        }
+    } else {
+        // lanes that added nothing hold job -1 and sum 0; with one job they
+        // join the others so that the warp adds with one atomic
+        job_add64(acc.sum, jobs == 1 ? 0 : acc.job, acc.base, acc.stride);
+    }
+}
+static_assert(sizeof(JobState) % sizeof(long long) == 0, "JobState must be a multiple of 8 bytes");
 
 // Count stored under key (0 if absent).  Read-only use during a kernel that
 // does not modify the table, so the non-coherent path is allowed.
@@ -202,31 +334,72 @@ __device__ __forceinline__ long long table_find_or_insert(Slot* t, unsigned long
     return -1;
 }
 
-// ---- launch wrappers (setup.cu) ----
-cudaError_t launch_validate(int n, long long nnz, const long long* off, const int* col, DevState* st,
-                            cudaStream_t s);
-cudaError_t launch_fill_src(int n, const long long* off, int* src, cudaStream_t s);
-cudaError_t launch_compact_labels(int n, int k, int kp, int lshift, const int* labels, int* G, void* lmap,
-                                  unsigned long long lmask, DevState* st, cudaStream_t s);
+// ---- setup.cu ----
+// Union assembly: per-job inputs were copied into staging buffers (offsets of
+// job j at offstage[vo_j + j ..], n_j + 1 entries; columns job-local at
+// col[eo_j ..]); these kernels validate them, build the union offsets, the
+// source array and the job of each vertex, and shift the columns to union ids.
+struct AssemblyArgs {
+    int jobs;
+    long long n, nnz;
+    const long long* offstage;  // N + J entries
+    const long long* eo;        // J + 1: first CSR entry of each job
+    const JobInfo* job;
+    long long* off;             // N + 1
+    int* col;                   // NNZ, job-local on entry, union ids on exit
+    int* src;
+    int* jid;
+    DevState* st;
+};
+cudaError_t launch_assemble(const AssemblyArgs& a, cudaStream_t s);
+// Second half of the assembly (source array, union columns), once the offsets are valid.
+cudaError_t launch_assemble_edges(const AssemblyArgs& a, cudaStream_t s);
+
+// Label compaction of all jobs: labels staged partition-major per job (job j's
+// k_j x n_j block at lo_j); pjob maps a global partition index (sum of the
+// earlier k plus i) to its job, pfirst the job to its first global partition.
+struct LabelArgs {
+    int jobs;
+    long long total;            // sum_j k_j n_j
+    const int* labels;          // staged labels
+    const long long* lo;        // J + 1: first staged label of each job
+    const int* pjob;            // global partition -> job
+    const int* pfirst;          // J: first global partition of each job
+    const JobInfo* job;
+    JobState* js;
+    int* G;
+    void* lmap;                 // 16-byte slots, lmask + 1 of them
+    unsigned long long lmask;
+    long long rows;             // entries of G
+    DevState* st;
+};
+cudaError_t launch_compact_labels(const LabelArgs& a, cudaStream_t s);
+
 cudaError_t launch_init_state(const SweepArgs& a, cudaStream_t s);
-// Summary rows of the singleton start ({g_i(v), 1, 0} for cluster v).
-cudaError_t launch_singleton_summaries(const SweepArgs& a, cudaStream_t s);
+// Summary rows of the singleton start ({g_i(v), 1, 0} for cluster v, padding {-1, 0, 0}).
+cudaError_t launch_singleton_summaries(const SweepArgs& a, long long rows, cudaStream_t s);
+// Sizes from C (ids outside their job set CC_ERR_INVALID).
 cudaError_t launch_state_from_ids(const SweepArgs& a, cudaStream_t s);
-// Rebuild of the table from C into st->new_mask + 1 slots, then st->mask = st->new_mask.
-// conditional: only if st->rebuild is set (decided on the device).
-cudaError_t launch_table_rebuild(const SweepArgs& a, bool conditional, cudaStream_t s);
+// Rebuild of the table and summary rows from C into st->new_mask + 1 slots,
+// then st->mask = st->new_mask.  conditional: only if st->rebuild is set.
+// eval: in a heavy sweep, also add the table part of F' to each job's recompute.
+cudaError_t launch_table_rebuild(const SweepArgs& a, long long rows, bool conditional, cudaStream_t s,
+                                 bool eval = false);
+// F of every job from scratch into js[j].recompute (without sum_ij |P_ij|^2).
 cudaError_t launch_objective_recompute(const SweepArgs& a, cudaStream_t s);
 
 // ---- api.cu ----
 // Message reported by cc_last_error(NULL) in this thread.
 void set_thread_error(const std::string& msg);
 
-// ---- launch wrappers (sweep.cu) ----
-cudaError_t launch_run_begin(DevState* st, int limit, cudaStream_t s);
-// One sweep (13 kernels); prop0/prop1 (may be null) are recorded around the proposal kernel.
+// ---- sweep.cu ----
+cudaError_t launch_run_begin(const SweepArgs& a, int limit, cudaStream_t s);
+// One sweep of every job; prop0/prop1 (may be null) are recorded around the
+// proposal kernels.
 constexpr int kKernelsPerRebuild = 11;
-constexpr int kKernelsPerSweep = 18 + 3 * kKernelsPerRebuild;
-cudaError_t launch_sweep(const SweepArgs& a, int grid, cudaStream_t s, cudaEvent_t prop0, cudaEvent_t prop1);
-cudaError_t prepare_propose(int kp, int* blocks_per_sm);
+constexpr int kKernelsPerSweep = 19 + 3 * kKernelsPerRebuild;
+cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaEvent_t prop0,
+                         cudaEvent_t prop1);
+cudaError_t prepare_propose(int* blocks_per_sm);
 
 }  // namespace ccg

@@ -1,0 +1,138 @@
+// Host-side state of a context (cc_ctx) and the internal calls that the
+// served form (server.cu) builds on: sizing a set of jobs before creating it,
+// creating a context from a memory pool, and running it without blocking.
+#pragma once
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "cc_internal.cuh"
+
+// A run of `limit` sweeps unrolled into one graph, with events at every sweep
+// boundary and around every proposal step.
+struct RunGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> bound;    // limit + 1
+    std::vector<cudaEvent_t> prop;     // 2 * limit
+};
+
+struct cc_ctx {
+    int jobs = 0, kmax = 0;
+    long long n = 0, nnz = 0, rows = 0, keys = 0;
+    int device = 0, sms = 0;
+    cudaStream_t stream = nullptr;      // stream used by calls
+    cudaStream_t own_stream = nullptr;  // stream created by the context (also used for capture)
+    cudaMemPool_t pool = nullptr;       // device memory comes from this pool (stream-ordered) if set
+    std::vector<ccg::JobInfo> job;      // host copy of the job table
+    std::vector<long long> F0;          // objective of each job at the singleton start
+    std::vector<long long> psq;         // sum_ij |P_ij|^2 of each job
+    ccg::JobInfo* d_job = nullptr;
+    ccg::JobState* js = nullptr;
+    long long* off = nullptr;
+    int* col = nullptr;
+    int* src = nullptr;
+    int* jid = nullptr;
+    int* G = nullptr;
+    int4* summ = nullptr;
+    int* C = nullptr;
+    int* size = nullptr;
+    int* dsize = nullptr;
+    unsigned long long* best = nullptr;
+    int* aown = nullptr;
+    ccg::Slot* table = nullptr;
+    int* pv = nullptr;
+    int* pa = nullptr;
+    int* pb = nullptr;
+    int* pg = nullptr;
+    unsigned char* pflag = nullptr;
+    int* members = nullptr;             // rebuild scratch (n)
+    int* cursor = nullptr;              // rebuild scratch (n)
+    int* bsum = nullptr;                // rebuild scratch (n/1024 + 2)
+    int* scratch = nullptr;             // 3n + n/1024 + 64 ints: output renumbering, warm starts
+    ccg::DevState* st = nullptr;
+    cc_sweep_info* hist = nullptr;
+    int hist_cap = 0;
+    ccg::SweepArgs args{};
+    std::map<int, RunGraph> graphs;
+    std::vector<float> sweep_ms;        // device time of each sweep of the last run
+    std::vector<float> propose_ms;      // ... and of its proposal kernels
+    long long launches = 0;             // kernels launched so far
+    int grid = 0;
+    unsigned long long cap_start = 0;   // active table capacity at the singleton start
+    unsigned long long cap_max = 0;     // allocated table capacity
+    bool started = false;               // start_state ran once
+    cc_options opt{};
+    std::vector<void*> allocs;
+    size_t bytes = 0;                   // device bytes held
+    std::string err;
+    // a run driven without blocking (ctx_async_*)
+    ccg::DevState* hstate = nullptr;    // pinned host copy of st, owned by the caller
+    cudaEvent_t chunk_done = nullptr;   // recorded after each graph launch and the copy of st
+    int async_limit = 0;
+    int async_launches = 0;
+};
+
+namespace ccg {
+
+// One input job, pointers host or device.
+struct JobInput {
+    int32_t n;
+    int64_t nnz;
+    const int64_t* row_off;
+    const int32_t* col;
+    int32_t k;
+    const int32_t* labels;
+};
+
+// Sizes of a context for a set of jobs, and the device bytes it holds.
+struct Plan {
+    int jobs = 0, kmax = 0, hist_cap = 0;
+    long long n = 0, nnz = 0, rows = 0, keys = 0, parts = 0;
+    unsigned long long cap_max = 0, cap_start = 0, lcap = 0;
+    size_t persistent = 0;  // held until cc_destroy
+    size_t temporary = 0;   // held during creation only
+};
+
+// Checks the sizes of the jobs and the options (host only; the data pointers
+// are not looked at) and sizes the context; *msg gets the reason of a failure.
+cc_status plan_jobs(int jobs, const JobInput* in, const cc_options& opt, Plan* out, std::string* msg);
+cc_status check_options(const cc_options& opt, std::string* msg);
+// Fills the capacities and byte counts of a plan from its totals (jobs, n,
+// nnz, rows, keys, parts, kmax).
+void finish_plan(Plan& p, const cc_options& opt);
+// Lanes that score one (vertex, candidate) pair for partitions of count k.
+int lanes_for_k(int k);
+
+// Options with the defaults filled in.
+cc_options resolve_options(const cc_options* opt);
+
+// cc_create / cc_batch_create with device memory from `pool` (stream-ordered
+// allocation on the context's own stream) when pool is not null.
+cc_status ctx_create(int jobs, const JobInput* in, bool on_device, const cc_options* opt, void* stream,
+                     cudaMemPool_t pool, cc_ctx** out);
+
+// Starts a run of at most `limit` sweeps without waiting: queues the run and
+// its first graph launch, then a copy of the control block into `pinned` and
+// an event.
+cc_status ctx_async_start(cc_ctx* c, int limit, DevState* pinned);
+
+// Checks a run started by ctx_async_start: 0 = still running (the next graph
+// launch is queued when the previous one ended without stopping), 1 = every
+// job has stopped, -1 = failed (*st holds the status).
+int ctx_async_poll(cc_ctx* c, cc_status* st);
+
+// Objective and sweeps of every job (synchronises the context's stream).
+cc_status ctx_job_results(cc_ctx* c, std::vector<long long>& F, std::vector<int>& sweeps);
+
+// Renumbered labels of job j into host memory (queued on the context's
+// stream; synchronise before reading).
+cc_status ctx_copy_labels(cc_ctx* c, const int* dev_labels, int j, int32_t* out);
+
+// Renumbers the labels of every job on the device; *dev_labels points into
+// the context's scratch.
+cc_status ctx_renumber(cc_ctx* c, int** dev_labels);
+
+void ctx_destroy(cc_ctx* c);
+
+}  // namespace ccg

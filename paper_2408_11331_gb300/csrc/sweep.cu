@@ -1,27 +1,29 @@
-// One synchronous local-move sweep (Methods, "Parallel algorithm"), as a fixed
-// sequence of kernels on one stream so that it can be captured in a CUDA graph:
+// One synchronous local-move sweep (Methods, "Parallel algorithm") of every
+// job of a context, as a fixed sequence of kernels on one stream so that it
+// can be captured in a CUDA graph:
 //
-//   begin       per-sweep counters; the sweep is skipped once the run has stopped
-//   own/edges/  best move of every vertex against the sweep-start state
-//   collect     (Eq. objective4 with the gain of Eq. objective3): A_a per
-//               vertex, then one lane group per CSR entry bidding its move,
-//               then the proposal list
-//   stage       singleton guard; stage the size and count deltas of the kept
-//               proposals P1 in the table (inserting target keys)
-//   eval        exact dF of applying P1 at once, from the staged deltas
-//   decide      commit P1 if dF < 0, else fall back to the matching of P
-//   commit      fold the staged deltas in (P1), or clear them and bid for the
-//               matching (fallback)
-//   match_*     commit the proposals that hold the least (dD, v) at both ends
-//   end         objective, history record, stop and rebuild decisions
-//   rebuild     (conditional) rebuild the contingency hash without dead keys
+//   begin        per-sweep counters (union-wide and per job); the sweep is
+//                skipped once every job has stopped
+//   own/edges/   best move of every vertex against the sweep-start state
+//   collect      (Eq. objective4 with the gain of Eq. objective3): A_a per
+//                vertex, then one lane group per CSR entry bidding its move,
+//                then the proposal list
+//   route        heavy or light evaluation of the kept moves P1 (results agree)
+//   heavy path   apply P1, rebuild the table, F' - F per job; commit, or undo and
+//                rebuild
+//   light path   singleton guard; stage size and count deltas; exact dF per job
+//   decide       per job: commit P1 if dF < 0, else the matching of P
+//   bid          matching jobs: drop staged deltas, bid (dD, v) at both clusters
+//   match_keys   winners (least (dD, v) at both ends) insert their target keys
+//   commit       fold staged deltas in (light P1), move the matching winners
+//   end          objective, history, stop per job; retry / compaction decisions
+//   rebuild      (conditional) rebuild of the contingency hash
 //
-// Gain of v moving from its cluster a to b (Eq. objective3, u = v excluded):
+// Gain of v moving from its cluster a to b (Eq. objective3, u = v excluded),
+// with k the number of partitions of v's job:
 //   dD = 2 (A_a - k - A_b) - k (|a| - 1 - |b|),   A_x = sum_i n(x, i, l_i(v)),
-// and the move changes F by 2 dD.  For a singleton candidate {u}, A_x is the
-// number of partitions in which u and v agree, read from u's label row; other
-// candidates take k probes of the contingency hash.
-#include "cc_internal.cuh"
+// and the move changes the job's F by 2 dD.
+#include "context.cuh"
 
 namespace ccg {
 
@@ -47,19 +49,11 @@ __device__ __forceinline__ long long warp_sum64(long long x)
     return x;
 }
 
-__device__ void block_add64(long long x, long long* out)
+// Adds the warp's sum of x to *out (one atomic).  All lanes must call it.
+__device__ __forceinline__ void warp_add64(long long x, long long* out)
 {
-    __shared__ long long part[32];
     x = warp_sum64(x);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) part[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        long long y = lane < (int)(blockDim.x >> 5) ? part[lane] : 0;
-        y = warp_sum64(y);
-        if (lane == 0 && y != 0) atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)y);
-    }
-    __syncthreads();
+    if ((threadIdx.x & 31) == 0 && x != 0) atomicAdd(reinterpret_cast<unsigned long long*>(out), (unsigned long long)x);
 }
 
 // Count under key given the slot h = hash(key) & mask already loaded as e.
@@ -75,24 +69,44 @@ __device__ __forceinline__ int resolve(const Slot* t, unsigned long long mask, u
     return 0;
 }
 
-__global__ void k_run_begin(DevState* st, int limit)
+__global__ void k_run_begin(SweepArgs a, int limit)
 {
-    st->stop = 0;
-    st->run_sweeps = 0;
-    st->run_limit = limit;
+    DevState* st = a.st;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->stop = 0;
+        st->run_limit = limit;
+        st->run_bodies = 0;
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.jobs; j += gridDim.x * blockDim.x) {
+        a.js[j].stop = 0;
+        a.js[j].run_sweeps = 0;
+    }
 }
 
-__global__ void k_begin(DevState* st)
+__global__ void k_begin(SweepArgs a)
 {
-    st->skip = (st->stop || st->err) ? 1 : 0;
-    st->overflow = 0;
-    st->nprop = 0;
-    st->np1 = 0;
-    st->dF = 0;
-    st->dF_p1 = 0;
-    st->moves = 0;
-    st->tile_ctr = 0;
-    st->mode = 0;
+    DevState* st = a.st;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->skip = (st->stop || st->err) ? 1 : 0;
+        st->nprop = 0;
+        st->pkeys = 0;
+        st->overflow = 0;
+        st->tile_ctr = 0;
+        st->heavy = 0;
+        st->rollback = 0;
+        st->active = 0;
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.jobs; j += gridDim.x * blockDim.x) {
+        JobState& s = a.js[j];
+        s.nprop = 0;
+        s.np1 = 0;
+        s.moves = 0;
+        s.dF = 0;
+        s.dF_p1 = 0;
+        s.mode = 0;
+        s.rollback = 0;
+        s.recompute = 0;
+    }
 }
 
 constexpr int kInflight = 4;  // loads per lane issued before the first is used
@@ -103,18 +117,17 @@ __device__ __forceinline__ int group_sum(int x, int gs)
     return x;
 }
 
-// Summary part of A_x(v) for a non-singleton cluster x, lanes of a group over
-// the partitions i = l, l + gs, ...: ex = sum of m where v carries the row's
-// label d (exact there), ub = ex + sum of m2 elsewhere (an upper bound on
-// A_x), nq = number of partitions where v does not carry d.
-__device__ __forceinline__ void summary_part(const SweepArgs& a, const int* __restrict__ gv, int x, int l, int gs,
-                                             int& ex, int& ub, int& nq)
+// Summary part of A_x(v) for a non-singleton cluster x of job J, lanes of a
+// group over the partitions i = l, l + gs, ...: ex = sum of m where v carries
+// the row's label d (exact there), ub = ex + sum of m2 elsewhere (an upper
+// bound on A_x).
+__device__ __forceinline__ void summary_part(const SweepArgs& a, const JobInfo& J, const int* __restrict__ gv, int x,
+                                             int l, int gs, int& ex, int& ub)
 {
     ex = 0;
     ub = 0;
-    nq = 0;
-    const int4* S = a.summ + (long long)x * a.kp;
-    for (int i0 = l; i0 < a.k; i0 += gs * kInflight) {
+    const int4* S = a.summ + row_of(J, x);
+    for (int i0 = l; i0 < J.k; i0 += gs * kInflight) {
         int4 r[kInflight];
         int g[kInflight];
 #pragma unroll
@@ -122,18 +135,17 @@ __device__ __forceinline__ void summary_part(const SweepArgs& a, const int* __re
             const int i = i0 + b * gs;
             r[b] = make_int4(-1, 0, 0, 0);
             g[b] = -2;
-            if (i < a.k) {
+            if (i < J.k) {
                 r[b] = __ldg(S + i);
                 g[b] = __ldg(gv + i);
             }
         }
 #pragma unroll
         for (int b = 0; b < kInflight; ++b) {
-            if (i0 + b * gs < a.k) {
+            if (i0 + b * gs < J.k) {
                 const bool eq = g[b] == r[b].x;
                 ex += eq ? r[b].y : 0;
                 ub += eq ? r[b].y : r[b].z;
-                nq += eq ? 0 : 1;
             }
         }
     }
@@ -141,12 +153,12 @@ __device__ __forceinline__ void summary_part(const SweepArgs& a, const int* __re
 
 // Exact counts of the partitions the summary leaves open (v does not carry
 // the row's label and another label may be present), by hash probes.
-__device__ __forceinline__ int probe_part(const SweepArgs& a, const Slot* __restrict__ table, unsigned long long mask,
-                                          const int* __restrict__ gv, int x, int l, int gs)
+__device__ __forceinline__ int probe_part(const SweepArgs& a, const JobInfo& J, const Slot* __restrict__ table,
+                                          unsigned long long mask, const int* __restrict__ gv, int x, int l, int gs)
 {
-    const int4* S = a.summ + (long long)x * a.kp;
+    const int4* S = a.summ + row_of(J, x);
     int acc = 0;
-    for (int i0 = l; i0 < a.k; i0 += gs * kInflight) {
+    for (int i0 = l; i0 < J.k; i0 += gs * kInflight) {
         unsigned long long key[kInflight], h[kInflight];
         ulonglong2 ev[kInflight];
         bool on[kInflight];
@@ -157,7 +169,7 @@ __device__ __forceinline__ int probe_part(const SweepArgs& a, const Slot* __rest
             key[b] = 0;
             h[b] = 0;
             ev[b] = make_ulonglong2(kEmpty, 0ull);
-            if (i < a.k) {
+            if (i < J.k) {
                 const int4 r = __ldg(S + i);
                 const int g = __ldg(gv + i);
                 on[b] = g != r.x && r.z > 0;
@@ -176,12 +188,11 @@ __device__ __forceinline__ int probe_part(const SweepArgs& a, const Slot* __rest
 }
 
 // Partitions in which u and v carry the same label, plus the padding entries
-// of this lane's quads: the two label rows compared as int4 quads.
-__device__ __forceinline__ int row_part(const SweepArgs& a, int u, int v, int l, int gs)
+// of this lane's quads: the two label rows (kq quads each) compared as int4.
+__device__ __forceinline__ int row_part(const int* gu_row, const int* gv_row, int kq, int l, int gs)
 {
-    const int4* gu = reinterpret_cast<const int4*>(a.G + (long long)u * a.kp);
-    const int4* gw = reinterpret_cast<const int4*>(a.G + (long long)v * a.kp);
-    const int kq = a.kp >> 2;
+    const int4* gu = reinterpret_cast<const int4*>(gu_row);
+    const int4* gw = reinterpret_cast<const int4*>(gv_row);
     int acc = 0;
     for (int q0 = l; q0 < kq; q0 += gs * kInflight) {
         int4 r[kInflight], s[kInflight];
@@ -202,7 +213,8 @@ __device__ __forceinline__ int row_part(const SweepArgs& a, int u, int v, int l,
     return acc;  // includes the kp - k padding entries (-1 in every row)
 }
 
-// Lanes per vertex (k_own) or per edge (k_edges): about five partitions per lane.
+// Lanes per vertex (k_own) or per edge (k_edges): about five partitions per
+// lane for the largest k of the context.
 __host__ __device__ __forceinline__ int lanes_per_item(int k)
 {
     int gs = 1;
@@ -210,66 +222,77 @@ __host__ __device__ __forceinline__ int lanes_per_item(int k)
     return gs;
 }
 
-// A_a for every vertex: k for a singleton, else the summary part of its own
-// cluster plus probes of the open partitions.  One group of lanes per vertex.
-__global__ void __launch_bounds__(kBlock) k_own(SweepArgs a)
+// A_a for every vertex of a running job: k for a singleton, else the summary
+// part of its own cluster plus probes of the open partitions.  One group of
+// lanes per vertex.
+// kSingle: the context holds one job, so every vertex belongs to job 0 and
+// the job is running whenever the sweep is not skipped.
+template <bool kSingle>
+__global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip) return;
     const unsigned long long mask = st->mask;
-    const int gs = lanes_per_item(a.k);
+    const int gs = lanes_per_item(a.kmax);
     const int lane = threadIdx.x & 31, l = lane & (gs - 1);
     const long long groups = (long long)gridDim.x * blockDim.x / gs;
+    const JobInfo J0 = a.job[0];
     for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x - lane) / gs; base < a.n;
          base += groups) {
         const long long v = base + lane / gs;
         const bool valid = v < a.n;
-        const int cv = valid ? __ldg(a.C + v) : 0;
-        const int sa = valid ? __ldg(a.size + cv) : 1;
-        const int* gv = a.G + (valid ? v : 0) * (long long)a.kp;
-        int ex = 0, ub = 0, nq = 0, pb = 0;
+        const int j = (kSingle || !valid) ? 0 : __ldg(a.jid + v);
+        const JobInfo J = kSingle ? J0 : a.job[j];
+        const bool on = valid && (kSingle || !a.js[j].stop);
+        const int cv = on ? __ldg(a.C + v) : 0;
+        const int sa = on ? __ldg(a.size + cv) : 1;
+        const int* gv = a.G + row_of(J, on ? v : J.vo);
+        int ex = 0, ub = 0, pb = 0;
         if (sa > 1) {
-            summary_part(a, gv, cv, l, gs, ex, ub, nq);
-            pb = probe_part(a, a.table, mask, gv, cv, l, gs);
+            summary_part(a, J, gv, cv, l, gs, ex, ub);
+            pb = probe_part(a, J, a.table, mask, gv, cv, l, gs);
         }
         const int A = group_sum(ex + pb, gs);
-        if (valid && l == 0) a.aown[v] = sa > 1 ? A : a.k;
+        if (on && l == 0) a.aown[v] = sa > 1 ? A : J.k;
     }
 }
 
 // Foreign CSR entries of one warp, compacted in shared memory.
 struct EdgeScratch {
-    int v[32], u[32], x[32], sx[32], sa[32], Aa[32];
+    int v[32], u[32], x[32], sx[32], sa[32], Aa[32], j[32];
 };
 
 // CSR entries 32 at a time per warp: each lane reads one entry (v, u) and
-// keeps it if u lies in another cluster than v (self-loops and repeats of the
-// same (v, C[u]) inside the warp are dropped); the kept entries are then
-// scored by groups of lanes.  A singleton {u} is scored from the two label
-// rows; another cluster from its summary rows, then (unless the lower bound on
-// dD from the summary is already >= 0) from probes of the open partitions.  A
-// move with dD < 0 bids its packed (dD, C[u]) at best[v] with an atomic
-// minimum.  All group reductions are outside the branches, so every lane of
-// the warp takes part in every shuffle.
+// keeps it if v's job runs and u lies in another cluster than v (self-loops
+// and repeats of the same (v, C[u]) inside the warp are dropped); the kept
+// entries are then scored by groups of lanes.  A singleton {u} is scored from
+// the two label rows; another cluster from its summary rows, then (unless the
+// lower bound on dD from the summary is already >= 0, in which case the move
+// can never be proposed) from probes of the open partitions.  A move with
+// dD < 0 bids its packed (dD, C[u]) at best[v] with an atomic minimum.  All
+// group reductions are outside the branches, so every lane of the warp takes
+// part in every shuffle.
+template <bool kSingle>
 __global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip) return;
     __shared__ EdgeScratch sh[kWarpsPerBlock];
     const unsigned long long mask = st->mask;
-    const int gs = lanes_per_item(a.k), per = 32 / gs;
+    const int gs = lanes_per_item(a.kmax), per = 32 / gs;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, l = lane & (gs - 1);
     const unsigned lt = (1u << lane) - 1u;
-    const int k = a.k, pad = a.kp - a.k;
     EdgeScratch& es = sh[w];
+    const JobInfo J0 = a.job[0];
     const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
     for (long long base = ((long long)blockIdx.x * kWarpsPerBlock + w) * 32; base < a.nnz; base += nwarps * 32) {
         const long long e = base + lane;
-        int v = 0, u = 0, x = -1;
+        int v = 0, u = 0, x = -1, j = 0;
         if (e < a.nnz) {
             v = __ldg(a.src + e);
+            if (!kSingle) j = __ldg(a.jid + v);
             u = __ldg(a.col + e);
-            if (u != v) {
+            if (u != v && (kSingle || !a.js[j].stop)) {
                 x = __ldg(a.C + u);
                 if (x == __ldg(a.C + v)) x = -1;
             }
@@ -284,6 +307,7 @@ __global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
             es.v[p] = v;
             es.u[p] = u;
             es.x[p] = x;
+            if (!kSingle) es.j[p] = j;
             es.sx[p] = __ldg(a.size + x);
             es.sa[p] = __ldg(a.size + cv);
             es.Aa[p] = __ldg(a.aown + v);
@@ -291,25 +315,27 @@ __global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
         __syncwarp();
         const int nf = __popc(km);
         for (int r0 = 0; r0 < nf; r0 += per) {
-            const int j = r0 + lane / gs;
-            const bool valid = j < nf;
-            const int ev = valid ? es.v[j] : 0, eu = valid ? es.u[j] : 0, ex_ = valid ? es.x[j] : 0;
-            const int sx = valid ? es.sx[j] : 0, sa = valid ? es.sa[j] : 0, Aa = valid ? es.Aa[j] : 0;
+            const int q = r0 + lane / gs;
+            const bool valid = q < nf;
+            const int ev = valid ? es.v[q] : 0, eu = valid ? es.u[q] : 0, ex_ = valid ? es.x[q] : 0;
+            const int sx = valid ? es.sx[q] : 0, sa = valid ? es.sa[q] : 0, Aa = valid ? es.Aa[q] : 0;
+            const JobInfo J = kSingle ? J0 : a.job[valid ? es.j[q] : 0];
+            const int k = J.k;
             const bool single = valid && sx == 1;
             const bool table = valid && sx > 1;
-            const int* gv = a.G + (long long)ev * a.kp;
-            int rc = 0, ex = 0, ub = 0, nq = 0;
-            if (single) rc = row_part(a, eu, ev, l, gs);
-            if (table) summary_part(a, gv, ex_, l, gs, ex, ub, nq);
+            const int* gv = a.G + row_of(J, valid ? ev : J.vo);
+            int rc = 0, ex = 0, ub = 0;
+            if (single) rc = row_part(a.G + row_of(J, eu), gv, J.kp >> 2, l, gs);
+            if (table) summary_part(a, J, gv, ex_, l, gs, ex, ub);
             rc = group_sum(rc, gs);
             ex = group_sum(ex, gs);
             ub = group_sum(ub, gs);
             const bool open = table && 2 * (Aa - k - ub) - k * (sa - 1 - sx) < 0;
             int pb = 0;
-            if (open) pb = probe_part(a, a.table, mask, gv, ex_, l, gs);
+            if (open) pb = probe_part(a, J, a.table, mask, gv, ex_, l, gs);
             pb = group_sum(pb, gs);
             if ((single || open) && l == 0) {
-                const int A = single ? rc - pad : ex + pb;
+                const int A = single ? rc - (J.kp - k) : ex + pb;
                 const int dD = 2 * (Aa - k - A) - k * (sa - 1 - sx);
                 if (dD < 0) atomicMin(&a.best[ev], pack_key(dD, ex_));
             }
@@ -318,156 +344,177 @@ __global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
     }
 }
 
-// Turns the bids into the proposal list (v, a, b, dD) and clears best[].
-// Each block gathers its proposals in shared memory and appends them with one
-// global atomic.
+// Turns the bids into the proposal list (v, a, b, dD), counts them per job and
+// clears best[].  Each block gathers its proposals in shared memory and
+// appends them with one global atomic.
 __global__ void __launch_bounds__(kBlock) k_collect(SweepArgs a)
 {
+    extern __shared__ long long dyn_jobs[];
     DevState* st = a.st;
     if (st->skip) return;
     __shared__ int4 sbuf[kBlock];
-    __shared__ int s_cnt;
+    __shared__ int s_cnt, s_keys;
     __shared__ unsigned long long s_base;
+    JobAcc acc(job_smem_init(a.jobs, dyn_jobs), reinterpret_cast<long long*>(&a.js[0].nprop), kJobStride);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < a.n; b0 += stride) {
-        if (threadIdx.x == 0) s_cnt = 0;
+        if (threadIdx.x == 0) {
+            s_cnt = 0;
+            s_keys = 0;
+        }
         __syncthreads();
         const long long v = b0 + threadIdx.x;
         if (v < a.n) {
             const unsigned long long key = a.best[v];
             if (key != kEmpty) {
                 a.best[v] = kEmpty;
+                const int job = a.jid[v];
+                acc.add(job, 1);
                 const int p = atomicAdd(&s_cnt, 1);
+                atomicAdd(&s_keys, a.job[job].k);
                 sbuf[p] = make_int4((int)v, a.C[v], (int)(unsigned)(key & 0xffffffffull), key_gain(key));
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0 && s_cnt > 0) s_base = atomicAdd(&st->nprop, (unsigned long long)s_cnt);
+        if (threadIdx.x == 0 && s_cnt > 0) {
+            s_base = atomicAdd(&st->nprop, (unsigned long long)s_cnt);
+            atomicAdd(&st->pkeys, (unsigned long long)s_keys);
+        }
         __syncthreads();
         for (int p = threadIdx.x; p < s_cnt; p += blockDim.x) {
             const int4 q = sbuf[p];
-            const unsigned long long j = s_base + p;
-            a.pv[j] = q.x;
-            a.pa[j] = q.y;
-            a.pb[j] = q.z;
-            a.pg[j] = q.w;
+            const unsigned long long jj = s_base + p;
+            a.pv[jj] = q.x;
+            a.pa[jj] = q.y;
+            a.pb[jj] = q.z;
+            a.pg[jj] = q.w;
         }
         __syncthreads();
     }
+    job_acc_finish(acc, a.jobs);
 }
 
 // ---- heavy sweeps --------------------------------------------------------
-// When a large share of the vertices proposes (|P| > n / 8, or always with
-// sweep_mode 2, never with sweep_mode 1), or the table
-// does not hold the counts of C yet (the singleton start), dF(P1) is taken
-// from a rebuild instead of from staged deltas: P1 is applied to C in place
-// (the movers' old clusters stay in the proposal list), the table and its
-// summary rows are rebuilt from the new C, and F' - F is dF(P1) exactly.  If
-// it is negative, P1 is committed as it stands (mode 3); otherwise the moves
-// are undone, the table is rebuilt from C again and the matching fallback
-// runs as in a light sweep (mode 2).
+// When the proposals move a large share of the label rows (more than 1/8 of
+// sum_j k_j n_j; for one job |P| > n / 8), or always with sweep_mode 2, never
+// with sweep_mode 1, or when the table does not hold the
+// counts of C yet (the singleton start), dF(P1) is taken from a rebuild
+// instead of from staged deltas: P1 is applied to C in place (the movers' old
+// clusters stay in the proposal list), the table and its summary rows are
+// rebuilt from the new C, and F' - F is dF(P1) exactly for every job.  A job
+// whose dF is negative has committed P1 (mode 3); any other job's moves are
+// undone, the table is rebuilt from C again and its matching fallback runs as
+// in a light sweep (mode 2).
 
 __global__ void k_route(SweepArgs a)
 {
+    const unsigned long long total_keys = a.keys;
     DevState* st = a.st;
     st->heavy = 0;
-    st->rollback = 0;
     if (st->skip || st->err || st->nprop == 0) return;
-    const bool light = a.sweep_mode == 1 || (a.sweep_mode == 0 && st->nprop * 8 <= (unsigned long long)a.n);
+    // light when the proposals move at most 1/8 of all label rows (for one
+    // job: |P| <= n / 8)
+    const bool light = a.sweep_mode == 1 || (a.sweep_mode == 0 && st->pkeys * 8 <= total_keys);
     if (st->tvalid && light) return;
     st->heavy = 1;
-    st->recompute = 0;
     // keys after applying P1: every vertex gives at most k, every mover at most k new ones
-    const unsigned long long kn = (unsigned long long)a.k * a.n;
-    unsigned long long bound = (st->tvalid ? (unsigned long long)st->live : kn) + (unsigned long long)a.k * st->nprop;
-    if (bound > kn) bound = kn;
+    unsigned long long bound = (st->tvalid ? (unsigned long long)st->live : total_keys) +
+                               st->pkeys;
+    if (bound > total_keys) bound = total_keys;
     unsigned long long c = a.cap_min;
     while (c < 2 * bound && c < a.mask_max + 1) c <<= 1;
     st->new_mask = c - 1;
     st->rebuild = 1;
 }
 
-// Singleton guard on every proposal (sizes of the sweep start); counts |P1|.
+// Singleton guard on every proposal (sizes of the sweep start); counts |P1| per job.
 __global__ void k_h_mark(SweepArgs a)
 {
+    extern __shared__ long long dyn_jobs[];
     DevState* st = a.st;
     if (st->skip || !st->heavy) return;
+    JobAcc acc(job_smem_init(a.jobs, dyn_jobs), reinterpret_cast<long long*>(&a.js[0].np1), kJobStride);
     const long long np = (long long)st->nprop;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
-        const long long j = base + threadIdx.x;
-        bool keep = false;
-        if (j < np) {
-            const int ca = a.pa[j], cb = a.pb[j];
-            keep = !(a.size[ca] == 1 && a.size[cb] == 1) || cb < ca;
-            a.pflag[j] = keep ? 1 : 0;
-        }
-        const unsigned mk = __ballot_sync(kFull, keep);
-        if (lane == 0 && mk) atomicAdd(&st->np1, (unsigned long long)__popc(mk));
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+        const int ca = a.pa[p], cb = a.pb[p];
+        const bool keep = !(a.size[ca] == 1 && a.size[cb] == 1) || cb < ca;
+        a.pflag[p] = keep ? 1 : 0;
+        if (keep) acc.add(a.jid[a.pv[p]], 1);
     }
+    job_acc_finish(acc, a.jobs);
 }
 
-// Applies (sign +1) or undoes (sign -1) the kept proposals on C and the sizes.
+// Applies (undo = 0) or undoes (undo = 1, jobs that roll back only) the kept
+// proposals on C and the sizes.
 __global__ void k_h_apply(SweepArgs a, int undo)
 {
     DevState* st = a.st;
     if (st->skip || !st->heavy || (undo && !st->rollback)) return;
     const long long np = (long long)st->nprop;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
-        if (!a.pflag[j]) continue;
-        const int ca = a.pa[j], cb = a.pb[j];
-        a.C[a.pv[j]] = undo ? ca : cb;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+        if (!a.pflag[p]) continue;
+        const int v = a.pv[p];
+        if (undo && !a.js[a.jid[v]].rollback) continue;
+        const int ca = a.pa[p], cb = a.pb[p];
+        a.C[v] = undo ? ca : cb;
         atomicAdd(&a.size[ca], undo ? 1 : -1);
         atomicAdd(&a.size[cb], undo ? -1 : 1);
     }
 }
 
-// F' = k sum_c s_c^2 - 2 sum_keys n^2 (+ sum_ij |P_ij|^2, added in k_h_decide):
-// the table part was added by the summary pass of the rebuild, this adds the
-// size part.
+// The size part of F' per job (k sum_c s_c^2); the table part was added by the
+// summary pass of the rebuild.
 __global__ void k_h_eval(SweepArgs a)
 {
+    extern __shared__ long long dyn_jobs[];
     DevState* st = a.st;
     if (st->skip || !st->heavy || st->err) return;
+    JobAcc acc(job_smem_init(a.jobs, dyn_jobs), &a.js[0].recompute, kJobStride);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < a.n; b0 += stride) {
-        const long long t = b0 + threadIdx.x;
-        long long acc = 0;
-        if (t < a.n) {
-            const long long sz = a.size[t];
-            acc = (long long)a.k * sz * sz;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < a.n; c += stride) {
+        const long long sz = a.size[c];
+        if (sz > 0) {
+            const int job = a.jid[c];
+            acc.add(job, (long long)a.job[job].k * sz * sz);
         }
-        block_add64(acc, &st->recompute);
     }
+    job_acc_finish(acc, a.jobs);
 }
 
 __global__ void k_h_decide(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip || !st->heavy) return;
-    if (st->err) {
-        st->mode = 0;
-        return;
-    }
-    const long long dF = st->recompute + st->partition_sq - st->F;
-    st->dF_p1 = st->np1 > 0 ? dF : 0;
-    if (st->np1 > 0 && dF < 0) {
-        st->mode = 3;
-        st->dF = dF;
-        st->moves = st->np1;
-    } else {
-        st->mode = 2;
-        st->dF = 0;
-        st->moves = 0;
-        if (st->np1 > 0) {
-            st->rollback = 1;
-            st->rebuild = 1;
-            st->new_mask = st->mask;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.jobs; j += gridDim.x * blockDim.x) {
+        JobState& s = a.js[j];
+        if (s.stop) continue;
+        if (st->err) {
+            s.mode = 0;
+            continue;
+        }
+        const long long dF = s.recompute + s.partition_sq - s.F;
+        s.dF_p1 = s.np1 > 0 ? dF : 0;
+        if (s.np1 > 0 && dF < 0) {
+            s.mode = 3;
+            s.dF = dF;
+            s.moves = s.np1;
+        } else {
+            s.mode = s.nprop > 0 ? 2 : 0;
+            s.dF = 0;
+            s.moves = 0;
+            if (s.np1 > 0) {
+                s.rollback = 1;
+                st->rollback = 1;
+                st->rebuild = 1;
+                st->new_mask = st->mask;
+            }
         }
     }
 }
+
+// ---- light sweeps -------------------------------------------------------
 
 // Occupancy above which a sweep is abandoned and retried in a larger table.
 __device__ __forceinline__ unsigned long long fill_limit(unsigned long long mask)
@@ -476,255 +523,318 @@ __device__ __forceinline__ unsigned long long fill_limit(unsigned long long mask
 }
 
 // Adds the warp's new slots to st->used and flags an overflow past the limit.
-__device__ __forceinline__ void count_inserts(DevState* st, unsigned mi, unsigned long long mask)
+// All lanes must call it.
+__device__ __forceinline__ void count_inserts(DevState* st, int mine, unsigned long long mask)
 {
-    if (mi) {
-        const unsigned long long old = atomicAdd(&st->used, (unsigned long long)__popc(mi));
-        if (old + __popc(mi) > fill_limit(mask)) st->overflow = 1;
+    int x = mine;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if ((threadIdx.x & 31) == 0 && x > 0) {
+        const unsigned long long old = atomicAdd(&st->used, (unsigned long long)x);
+        if (old + x > fill_limit(mask)) st->overflow = 1;
     }
 }
 
-// One thread per (proposal j, partition i).  Staging never fails: if the
-// table runs short of slots the sweep is abandoned (st->overflow) before
-// anything is committed, and k_end schedules a larger table and a retry.
+// Thread per proposal, over its job's partitions.  Staging never fails: if
+// the table runs short of slots the sweep is abandoned (st->overflow) before
+// anything is committed, and the sweep end schedules a larger table and a
+// retry.
 __global__ void k_stage(SweepArgs a)
 {
+    extern __shared__ long long dyn_jobs[];
     DevState* st = a.st;
     if (st->skip || st->err || st->heavy) return;
+    JobAcc acc(job_smem_init(a.jobs, dyn_jobs), reinterpret_cast<long long*>(&a.js[0].np1), kJobStride);
     const unsigned long long mask = st->mask;
-    const long long total = (long long)st->nprop * a.k;
+    const long long np = (long long)st->nprop;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-        const long long t = base + threadIdx.x;
-        bool ins = false, head = false;
-        if (t < total) {
-            const long long j = t / a.k;
-            const int i = (int)(t - j * a.k);
-            const int v = a.pv[j], ca = a.pa[j], cb = a.pb[j];
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+        const long long p = base + threadIdx.x;
+        int job = -1, ins_count = 0;
+        if (p < np) {
+            const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
             const bool keep = !(a.size[ca] == 1 && a.size[cb] == 1) || cb < ca;
-            if (i == 0) {
-                a.pflag[j] = keep ? 1 : 0;
-                if (keep) {
-                    atomicAdd(&a.dsize[ca], -1);
-                    atomicAdd(&a.dsize[cb], 1);
-                    head = true;
-                }
-            }
+            a.pflag[p] = keep ? 1 : 0;
             if (keep) {
-                const int g = a.G[(long long)v * a.kp + i];
-                const long long sa = table_find(a.table, mask, ckey(ca, g));
-                const long long sb = table_find_or_insert(a.table, mask, ckey(cb, g), &ins);
-                if (sa < 0) {
-                    set_err(st, CC_ERR_INVALID);  // the vertex's own key must exist
-                } else if (sb < 0) {
-                    st->overflow = 1;
-                } else {
-                    atomicAdd(&a.table[sa].dlt, -1);
-                    atomicAdd(&a.table[sb].dlt, 1);
-                    a.pslot[2 * t] = (unsigned)sa;
-                    a.pslot[2 * t + 1] = (unsigned)sb;
+                const int j = a.jid[v];
+                job = j;
+                const JobInfo& J = a.job[j];
+                atomicAdd(&a.dsize[ca], -1);
+                atomicAdd(&a.dsize[cb], 1);
+                const int* gv = a.G + row_of(J, v);
+                for (int i = 0; i < J.k; ++i) {
+                    const int g = gv[i];
+                    bool ins = false;
+                    const long long sa = table_find(a.table, mask, ckey(ca, g));
+                    const long long sb = table_find_or_insert(a.table, mask, ckey(cb, g), &ins);
+                    ins_count += ins;
+                    if (sa < 0) {
+                        set_err(st, CC_ERR_INVALID);  // the vertex's own key must exist
+                    } else if (sb < 0) {
+                        st->overflow = 1;
+                    } else {
+                        atomicAdd(&a.table[sa].dlt, -1);
+                        atomicAdd(&a.table[sb].dlt, 1);
+                    }
                 }
             }
         }
-        const unsigned mi = __ballot_sync(kFull, ins), mh = __ballot_sync(kFull, head);
-        if (lane == 0) {
-            count_inserts(st, mi, mask);
-            if (mh) atomicAdd(&st->np1, (unsigned long long)__popc(mh));
-        }
+        count_inserts(st, ins_count, mask);
+        if (job >= 0) acc.add(job, 1);
     }
+    job_acc_finish(acc, a.jobs);
 }
 
-// dF(P1) = k sum_c ((s+ds)^2 - s^2) - 2 sum_keys ((n+dn)^2 - n^2), written as a
-// sum over the staged contributions: each +-1 added to an entry x with final
-// delta d_x contributes +-(2 x + d_x).
+// dF(P1) per job = k sum_c ((s+ds)^2 - s^2) - 2 sum_keys ((n+dn)^2 - n^2),
+// written as a sum over the staged contributions: each +-1 added to an entry
+// x with final delta d_x contributes +-(2 x + d_x).
 __global__ void k_eval(SweepArgs a)
 {
+    extern __shared__ long long dyn_jobs[];
     DevState* st = a.st;
     if (st->skip || st->err || st->overflow || st->heavy) return;
-    const long long total = (long long)st->nprop * a.k;
+    JobAcc acc(job_smem_init(a.jobs, dyn_jobs), &a.js[0].dF, kJobStride);
+    const unsigned long long mask = st->mask;
+    const long long np = (long long)st->nprop;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-        const long long t = base + threadIdx.x;
-        long long acc = 0;
-        if (t < total) {
-            const long long j = t / a.k;
-            const int i = (int)(t - j * a.k);
-            if (a.pflag[j]) {
-                const ulonglong2 A = *reinterpret_cast<const ulonglong2*>(a.table + a.pslot[2 * t]);
-                const ulonglong2 B = *reinterpret_cast<const ulonglong2*>(a.table + a.pslot[2 * t + 1]);
-                const long long an = (int)(unsigned)(A.y & 0xffffffffull), ad = (int)(unsigned)(A.y >> 32);
-                const long long bn = (int)(unsigned)(B.y & 0xffffffffull), bd = (int)(unsigned)(B.y >> 32);
-                acc = -2 * (-(2 * an + ad) + (2 * bn + bd));
-                if (i == 0) {
-                    const int ca = a.pa[j], cb = a.pb[j];
-                    acc += (long long)a.k * (-(2LL * a.size[ca] + a.dsize[ca]) + (2LL * a.size[cb] + a.dsize[cb]));
-                }
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+        if (!a.pflag[p]) continue;
+        const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
+        const int job = a.jid[v];
+        const JobInfo& J = a.job[job];
+        const int* gv = a.G + row_of(J, v);
+        long long keys = 0;
+        for (int i = 0; i < J.k; ++i) {
+            const int g = gv[i];
+            const long long sa = table_find(a.table, mask, ckey(ca, g));
+            const long long sb = table_find(a.table, mask, ckey(cb, g));
+            if (sa < 0 || sb < 0) {
+                set_err(st, CC_ERR_INVALID);  // staged keys must exist
+                continue;
             }
+            const Slot* A = a.table + sa;
+            const Slot* B = a.table + sb;
+            keys += -(2LL * A->cnt + A->dlt) + (2LL * B->cnt + B->dlt);
         }
-        block_add64(acc, &st->dF);
+        acc.add(job, -2 * keys + (long long)J.k * (-(2LL * a.size[ca] + a.dsize[ca]) + (2LL * a.size[cb] + a.dsize[cb])));
     }
+    job_acc_finish(acc, a.jobs);
 }
 
-__global__ void k_decide(DevState* st)
+__global__ void k_decide(SweepArgs a)
 {
+    DevState* st = a.st;
     if (st->skip || st->heavy) return;
-    if (st->err || st->overflow) {
-        st->mode = 0;
-        return;
-    }
-    if (st->np1 > 0 && st->dF < 0) {
-        st->mode = 1;
-        st->dF_p1 = st->dF;
-        st->moves = st->np1;
-    } else if (st->nprop > 0) {
-        st->mode = 2;
-        st->dF_p1 = st->np1 > 0 ? st->dF : 0;
-        st->dF = 0;
-        st->moves = 0;
-    } else {
-        st->mode = 0;
-        st->dF = 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.jobs; j += gridDim.x * blockDim.x) {
+        JobState& s = a.js[j];
+        if (s.stop) continue;
+        if (st->err || st->overflow) {
+            s.mode = 0;
+            continue;
+        }
+        if (s.np1 > 0 && s.dF < 0) {
+            s.mode = 1;
+            s.dF_p1 = s.dF;
+            s.moves = s.np1;
+        } else if (s.nprop > 0) {
+            s.mode = 2;
+            s.dF_p1 = s.np1 > 0 ? s.dF : 0;
+            s.dF = 0;
+            s.moves = 0;
+        } else {
+            s.mode = 0;
+            s.dF = 0;
+        }
     }
 }
 
-__global__ void k_commit(SweepArgs a)
+// Thread per proposal of a job that falls back to the matching (mode 2):
+// undo its staged deltas (light sweeps) and bid its (dD, v) at both clusters.
+__global__ void k_bid(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip || st->err) return;
-    const int mode = st->mode;
-    if (mode == 0 || mode == 3) return;
-    const bool staged = !st->heavy;  // only light sweeps staged deltas to undo
-    const long long total = (long long)st->nprop * a.k;
+    const bool staged = !st->heavy;
+    const unsigned long long mask = st->mask;
+    const long long np = (long long)st->nprop;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-        const long long t = base + threadIdx.x;
-        long long live = 0;
-        if (t < total) {
-            const long long j = t / a.k;
-            const int i = (int)(t - j * a.k);
-            const int ca = a.pa[j], cb = a.pb[j];
-            if (mode == 1) {
-                if (a.pflag[j]) {
-                    if (i == 0) {
-                        a.C[a.pv[j]] = cb;
-                        int d = atomicExch(&a.dsize[ca], 0);
-                        if (d) atomicAdd(&a.size[ca], d);
-                        d = atomicExch(&a.dsize[cb], 0);
-                        if (d) atomicAdd(&a.size[cb], d);
-                    }
-#pragma unroll
-                    for (int side = 0; side < 2; ++side) {
-                        Slot* s = a.table + a.pslot[2 * t + side];
-                        const int d = atomicExch(&s->dlt, 0);
-                        if (d) {
-                            const int old = atomicAdd(&s->cnt, d);
-                            live += (old == 0) - (old + d == 0);
-                            summ_update(a.summ, a.kp, a.lshift, s->key, d, old + d);
-                        }
-                    }
-                }
-            } else {
-                if (staged && a.pflag[j]) {
-                    a.table[a.pslot[2 * t]].dlt = 0;
-                    a.table[a.pslot[2 * t + 1]].dlt = 0;
-                    if (i == 0) {
-                        a.dsize[ca] = 0;
-                        a.dsize[cb] = 0;
-                    }
-                }
-                if (i == 0) {
-                    const unsigned long long key = pack_key(a.pg[j], a.pv[j]);
-                    atomicMin(&a.best[ca], key);
-                    atomicMin(&a.best[cb], key);
-                }
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+        const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
+        const int j = a.jid[v];
+        if (a.js[j].mode != 2) continue;
+        if (staged && a.pflag[p]) {
+            const JobInfo& J = a.job[j];
+            const int* gv = a.G + row_of(J, v);
+            for (int i = 0; i < J.k; ++i) {
+                const int g = gv[i];
+                const long long sa = table_find(a.table, mask, ckey(ca, g));
+                const long long sb = table_find(a.table, mask, ckey(cb, g));
+                if (sa >= 0) a.table[sa].dlt = 0;
+                if (sb >= 0) a.table[sb].dlt = 0;
             }
+            a.dsize[ca] = 0;
+            a.dsize[cb] = 0;
         }
-        block_add64(live, &st->live);
+        const unsigned long long key = pack_key(a.pg[p], v);
+        atomicMin(&a.best[ca], key);
+        atomicMin(&a.best[cb], key);
     }
 }
 
 // Fallback: a proposal is committed iff its (dD, v) is the least at both of
 // its clusters; the committed moves touch pairwise-disjoint clusters, so
-// their objective changes add exactly.  Phase 1 (thread per (proposal,
-// partition)) marks the winners and inserts their target keys, so that an
-// overflow is seen before any count changes; phase 2 applies the moves.
+// their objective changes add exactly.  This pass marks the winners and
+// inserts their target keys.  It runs before any count of any job changes,
+// so that a table overflow abandons the whole sweep with nothing committed.
 __global__ void k_match_keys(SweepArgs a)
 {
     DevState* st = a.st;
-    if (st->skip || st->err || st->mode != 2) return;
+    if (st->skip || st->err) return;
     const unsigned long long mask = st->mask;
-    const long long total = (long long)st->nprop * a.k;
+    const long long np = (long long)st->nprop;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-        const long long t = base + threadIdx.x;
-        bool ins = false;
-        if (t < total) {
-            const long long j = t / a.k;
-            const int i = (int)(t - j * a.k);
-            const int v = a.pv[j], ca = a.pa[j], cb = a.pb[j];
-            const unsigned long long key = pack_key(a.pg[j], v);
-            if (a.best[ca] == key && a.best[cb] == key) {
-                if (i == 0) a.pflag[j] = 2;
-                const long long sb = table_find_or_insert(a.table, mask, ckey(cb, a.G[(long long)v * a.kp + i]), &ins);
-                if (sb < 0) st->overflow = 1;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+        const long long p = base + threadIdx.x;
+        int ins_count = 0;
+        if (p < np) {
+            const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
+            const int j = a.jid[v];
+            const unsigned long long key = pack_key(a.pg[p], v);
+            if (a.js[j].mode == 2 && a.best[ca] == key && a.best[cb] == key) {
+                a.pflag[p] = 2;
+                const JobInfo& J = a.job[j];
+                const int* gv = a.G + row_of(J, v);
+                for (int i = 0; i < J.k; ++i) {
+                    bool ins = false;
+                    if (table_find_or_insert(a.table, mask, ckey(cb, gv[i]), &ins) < 0) st->overflow = 1;
+                    ins_count += ins;
+                }
             }
         }
-        const unsigned mi = __ballot_sync(kFull, ins);
-        if (lane == 0) count_inserts(st, mi, mask);
+        count_inserts(st, ins_count, mask);
     }
 }
 
-__global__ void k_match_apply(SweepArgs a)
+// Thread per proposal: the light commit of P1 (mode 1: C, the staged size
+// and count deltas folded in) or the move of a matching winner (mode 2).
+// Skipped entirely after an overflow.
+__global__ void k_commit(SweepArgs a)
 {
+    extern __shared__ long long dyn_jobs[];
     DevState* st = a.st;
-    if (st->skip || st->err || st->overflow || st->mode != 2) return;
+    if (st->skip || st->err || st->overflow) return;
+    long long* sh = job_smem_init(2 * a.jobs <= kSmemJobs ? a.jobs : 0, dyn_jobs);
+    if (sh) {
+        for (int j = threadIdx.x; j < a.jobs; j += blockDim.x) sh[a.jobs + j] = 0;
+        __syncthreads();
+    }
+    JobAcc mv(sh, reinterpret_cast<long long*>(&a.js[0].moves), kJobStride);
+    JobAcc df(sh ? sh + a.jobs : nullptr, &a.js[0].dF, kJobStride);
     const unsigned long long mask = st->mask;
-    const long long total = (long long)st->nprop * a.k;
+    const long long np = (long long)st->nprop;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += stride) {
-        const long long t = base + threadIdx.x;
-        long long live = 0;
-        if (t < total) {
-            const long long j = t / a.k;
-            const int i = (int)(t - j * a.k);
-            if (a.pflag[j] == 2) {
-                const int v = a.pv[j], ca = a.pa[j], cb = a.pb[j];
-                if (i == 0) {
-                    a.C[v] = cb;
-                    atomicAdd(&a.size[ca], -1);
-                    atomicAdd(&a.size[cb], 1);
-                    atomicAdd(&st->moves, 1ull);
-                    atomicAdd(reinterpret_cast<unsigned long long*>(&st->dF), (unsigned long long)(2LL * a.pg[j]));
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
+        const long long p = base + threadIdx.x;
+        long long live = 0, dF = 0, moved = 0;
+        int job = -1;
+        if (p < np) {
+            const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
+            const int j = a.jid[v];
+            const int mode = a.js[j].mode;
+            const JobInfo& J = a.job[j];
+            const int* gv = a.G + row_of(J, v);
+            if (mode == 1 && a.pflag[p]) {
+                a.C[v] = cb;
+                int d = atomicExch(&a.dsize[ca], 0);
+                if (d) atomicAdd(&a.size[ca], d);
+                d = atomicExch(&a.dsize[cb], 0);
+                if (d) atomicAdd(&a.size[cb], d);
+                for (int i = 0; i < J.k; ++i) {
+                    const int g = gv[i];
+#pragma unroll
+                    for (int side = 0; side < 2; ++side) {
+                        const long long si = table_find(a.table, mask, ckey(side ? cb : ca, g));
+                        if (si < 0) {
+                            set_err(st, CC_ERR_INVALID);
+                            continue;
+                        }
+                        Slot* s = a.table + si;
+                        const int dd = atomicExch(&s->dlt, 0);
+                        if (dd) {
+                            const int old = atomicAdd(&s->cnt, dd);
+                            live += (old == 0) - (old + dd == 0);
+                            summ_update(a, s->key, dd, old + dd);
+                        }
+                    }
                 }
-                const int g = a.G[(long long)v * a.kp + i];
-                const long long sa = table_find(a.table, mask, ckey(ca, g));
-                const long long sb = table_find(a.table, mask, ckey(cb, g));
-                if (sa < 0 || sb < 0) {
-                    set_err(st, CC_ERR_INVALID);
-                } else {
+            } else if (mode == 2 && a.pflag[p] == 2) {
+                job = j;
+                a.C[v] = cb;
+                atomicAdd(&a.size[ca], -1);
+                atomicAdd(&a.size[cb], 1);
+                moved = 1;
+                dF = 2LL * a.pg[p];
+                for (int i = 0; i < J.k; ++i) {
+                    const int g = gv[i];
+                    const long long sa = table_find(a.table, mask, ckey(ca, g));
+                    const long long sb = table_find(a.table, mask, ckey(cb, g));
+                    if (sa < 0 || sb < 0) {
+                        set_err(st, CC_ERR_INVALID);
+                        continue;
+                    }
                     const int oa = atomicAdd(&a.table[sa].cnt, -1);
                     const int ob = atomicAdd(&a.table[sb].cnt, 1);
                     live += (ob == 0) - (oa == 1);
-                    summ_update(a.summ, a.kp, a.lshift, ckey(ca, g), -1, oa - 1);
-                    summ_update(a.summ, a.kp, a.lshift, ckey(cb, g), 1, ob + 1);
+                    summ_update(a, ckey(ca, g), -1, oa - 1);
+                    summ_update(a, ckey(cb, g), 1, ob + 1);
                 }
             }
         }
-        block_add64(live, &st->live);
+        warp_add64(live, &st->live);
+        if (job >= 0) {
+            mv.add(job, moved);
+            df.add(job, dF);
+        }
     }
+    job_acc_finish(mv, a.jobs);
+    job_acc_finish(df, a.jobs);
 }
 
 __global__ void k_match_reset(SweepArgs a)
 {
     DevState* st = a.st;
-    if (st->skip || st->mode != 2) return;
+    if (st->skip) return;
     const long long np = (long long)st->nprop;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
-        a.best[a.pa[j]] = kEmpty;
-        a.best[a.pb[j]] = kEmpty;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+        if (a.js[a.jid[a.pv[p]]].mode != 2) continue;
+        a.best[a.pa[p]] = kEmpty;
+        a.best[a.pb[p]] = kEmpty;
+    }
+}
+
+// Per job: objective, history record, stop.  An abandoned sweep changes no job.
+__global__ void k_end_jobs(SweepArgs a)
+{
+    DevState* st = a.st;
+    if (st->skip || st->err || st->overflow) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.jobs; j += gridDim.x * blockDim.x) {
+        JobState& s = a.js[j];
+        if (s.stop) continue;
+        if (s.mode != 0) s.F += s.dF;
+        if (s.sweeps < a.hist_cap) {
+            cc_sweep_info r;
+            r.proposals = (int64_t)s.nprop;
+            r.p1 = (int64_t)s.np1;
+            r.dF_p1 = s.dF_p1;
+            r.fallback = s.mode == 2 ? 1 : 0;
+            r.moves = (int64_t)s.moves;
+            r.F = s.F;
+            a.hist[(long long)j * a.hist_cap + s.sweeps] = r;
+        }
+        s.sweeps += 1;
+        s.run_sweeps += 1;
+        if (s.nprop == 0 || s.run_sweeps >= st->run_limit) s.stop = 1;
+        else atomicAdd(&st->active, 1);
     }
 }
 
@@ -732,6 +842,7 @@ __global__ void k_end(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip) return;
+    st->run_bodies += 1;
     if (st->err) {
         st->stop = 1;
         return;
@@ -739,8 +850,11 @@ __global__ void k_end(SweepArgs a)
     const unsigned long long cap = st->mask + 1;
     if (st->overflow) {
         // nothing was committed: retry this sweep after rebuilding into twice
-        // the capacity (the staged deltas are discarded with the old table)
-        if (cap >= a.mask_max + 1) {
+        // the capacity (the staged deltas are discarded with the old table).
+        // A heavy sweep sizes its table for every key it can create, so it
+        // cannot overflow; if it did, jobs that kept P1 have moved already
+        // and a retry would be wrong, so that is reported instead.
+        if (cap >= a.mask_max + 1 || st->heavy) {
             set_err(st, CC_ERR_TABLE_FULL);
             st->stop = 1;
             return;
@@ -751,27 +865,14 @@ __global__ void k_end(SweepArgs a)
         st->retries += 1;
         return;
     }
-    if (st->mode != 0) st->F += st->dF;
-    if (st->sweeps < a.hist_cap) {
-        cc_sweep_info r;
-        r.proposals = (int64_t)st->nprop;
-        r.p1 = (int64_t)st->np1;
-        r.dF_p1 = st->dF_p1;
-        r.fallback = st->mode == 2 ? 1 : 0;
-        r.moves = (int64_t)st->moves;
-        r.F = st->F;
-        a.hist[st->sweeps] = r;
-    }
-    st->sweeps += 1;
-    st->run_sweeps += 1;
-    if (st->nprop == 0 || st->run_sweeps >= st->run_limit) st->stop = 1;
+    st->stop = st->active == 0 ? 1 : 0;
     // compaction: rebuild without the dead keys when occupied slots pass one
     // half of the capacity; the new capacity holds the live keys plus k x
-    // (moves of this sweep), a forecast of the next sweep's new keys, at load
-    // <= 1/2.  (Summary rows settle most of each score, so a table larger than
-    // needed costs little; it is not shrunk otherwise.)
+    // (proposals of this sweep), a forecast of the next sweep's new keys, at
+    // load <= 1/2.  (Summary rows settle most of each score, so a table larger
+    // than needed costs little; it is not shrunk otherwise.)
     const unsigned long long live = (unsigned long long)st->live;
-    const unsigned long long want = 2 * (live + (unsigned long long)a.k * st->moves);
+    const unsigned long long want = 2 * (live + st->pkeys);
     unsigned long long c = a.cap_min;
     while (c < want && c < a.mask_max + 1) c <<= 1;
     if (st->tvalid && st->used > cap / 2) {
@@ -782,60 +883,79 @@ __global__ void k_end(SweepArgs a)
     }
 }
 
-}  // namespace
-
-cudaError_t prepare_propose(int kp, int* blocks_per_sm)
+inline int jobs_grid(int jobs)
 {
-    (void)kp;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_edges, kBlock, 0);
+    int g = (jobs + 255) / 256;
+    return g < 1 ? 1 : g;
 }
 
-cudaError_t launch_run_begin(DevState* st, int limit, cudaStream_t s)
+}  // namespace
+
+int lanes_for_k(int k)
 {
-    k_run_begin<<<1, 1, 0, s>>>(st, limit);
+    return lanes_per_item(k);
+}
+
+cudaError_t prepare_propose(int* blocks_per_sm)
+{
+    int single = 0, multi = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&single, k_edges<true>, kBlock, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&multi, k_edges<false>, kBlock, 0);
+    *blocks_per_sm = single < multi ? single : multi;
+    return e;
+}
+
+cudaError_t launch_run_begin(const SweepArgs& a, int limit, cudaStream_t s)
+{
+    k_run_begin<<<jobs_grid(a.jobs), 256, 0, s>>>(a, limit);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const SweepArgs& a, int grid, cudaStream_t s, cudaEvent_t prop0, cudaEvent_t prop1)
+cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaEvent_t prop0,
+                         cudaEvent_t prop1)
 {
     const int g2 = grid;
-    k_begin<<<1, 1, 0, s>>>(a.st);
+    const int jg = jobs_grid(a.jobs);
+    const size_t js1 = smem_jobs_bytes(a.jobs);
+    k_begin<<<jg, 256, 0, s>>>(a);
     if (prop0) {
         cudaError_t e = cudaEventRecordWithFlags(prop0, s, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
-    k_own<<<grid, kBlock, 0, s>>>(a);
-    k_edges<<<grid, kBlock, 0, s>>>(a);
-    k_collect<<<grid, kBlock, 0, s>>>(a);
+    if (a.jobs == 1) {
+        k_own<true><<<grid, kBlock, 0, s>>>(a);
+        k_edges<true><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        k_own<false><<<grid, kBlock, 0, s>>>(a);
+        k_edges<false><<<grid, kBlock, 0, s>>>(a);
+    }
+    k_collect<<<grid, kBlock, js1, s>>>(a);
     if (prop1) {
         cudaError_t e = cudaEventRecordWithFlags(prop1, s, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
     k_route<<<1, 1, 0, s>>>(a);
-    k_h_mark<<<g2, kBlock, 0, s>>>(a);
+    k_h_mark<<<g2, kBlock, js1, s>>>(a);
     k_h_apply<<<g2, kBlock, 0, s>>>(a, 0);
-    {
-        cudaError_t e = launch_table_rebuild(a, true, s);
-        if (e != cudaSuccess) return e;
-    }
-    k_h_eval<<<g2, kBlock, 0, s>>>(a);
-    k_h_decide<<<1, 1, 0, s>>>(a);
-    k_h_apply<<<g2, kBlock, 0, s>>>(a, 1);
-    {
-        cudaError_t e = launch_table_rebuild(a, true, s);
-        if (e != cudaSuccess) return e;
-    }
-    k_stage<<<g2, kBlock, 0, s>>>(a);
-    k_eval<<<g2, kBlock, 0, s>>>(a);
-    k_decide<<<1, 1, 0, s>>>(a.st);
-    k_commit<<<g2, kBlock, 0, s>>>(a);
-    k_match_keys<<<g2, kBlock, 0, s>>>(a);
-    k_match_apply<<<g2, kBlock, 0, s>>>(a);
-    k_match_reset<<<g2, kBlock, 0, s>>>(a);
-    k_end<<<1, 1, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_table_rebuild(a, rows, true, s, true);
     if (e != cudaSuccess) return e;
-    return launch_table_rebuild(a, true, s);
+    k_h_eval<<<g2, kBlock, js1, s>>>(a);
+    k_h_decide<<<jg, 256, 0, s>>>(a);
+    k_h_apply<<<g2, kBlock, 0, s>>>(a, 1);
+    e = launch_table_rebuild(a, rows, true, s);
+    if (e != cudaSuccess) return e;
+    k_stage<<<g2, kBlock, js1, s>>>(a);
+    k_eval<<<g2, kBlock, js1, s>>>(a);
+    k_decide<<<jg, 256, 0, s>>>(a);
+    k_bid<<<g2, kBlock, 0, s>>>(a);
+    k_match_keys<<<g2, kBlock, 0, s>>>(a);
+    k_commit<<<g2, kBlock, 2 * a.jobs <= kSmemJobs ? 2 * smem_jobs_bytes(a.jobs) : 0, s>>>(a);
+    k_match_reset<<<g2, kBlock, 0, s>>>(a);
+    k_end_jobs<<<jg, 256, 0, s>>>(a);
+    k_end<<<1, 1, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_table_rebuild(a, rows, true, s);
 }
 
 }  // namespace ccg

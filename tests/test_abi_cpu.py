@@ -91,3 +91,91 @@ def test_python_binding_checks_shapes(native):
         native.cc_create(np.zeros(3, np.int64), np.zeros(0, np.int32), np.zeros(4, np.int32))
     with pytest.raises(ValueError):
         native.cc_create(np.zeros(3, np.int64), np.zeros(0, np.int32), np.zeros((1, 4), np.int32))
+
+
+def test_batch_host_validation(native):
+    """cc_batch_create checks every job on the host before any device work."""
+    lib = native.lib
+    ctx = ctypes.c_void_p(123)
+    assert lib.cc_batch_create(0, None, None, ctypes.byref(ctx)) == 1
+    assert ctx.value is None
+    ok = 1
+    good = native.cc_job_desc(5, 0, ok, None, 2, ok)
+    descs = (native.cc_job_desc * 3)(good, good, native.cc_job_desc(0, 0, ok, None, 2, ok))
+    assert lib.cc_batch_create(3, descs, None, ctypes.byref(ctx)) == 1
+    assert "job 2" in native.cc_last_error(None)
+    descs = (native.cc_job_desc * 2)(good, native.cc_job_desc(5, 0, ok, None, 4097, ok))
+    assert lib.cc_batch_create(2, descs, None, ctypes.byref(ctx)) == 1
+    assert "job 1" in native.cc_last_error(None)
+    descs = (native.cc_job_desc * 2)(native.cc_job_desc(300_000_000, 0, ok, None, 3, ok), good)
+    assert lib.cc_batch_create(2, descs, None, ctypes.byref(ctx)) == 4
+    # a job count the union cannot index: 2^31 vertices in all
+    big = native.cc_job_desc(100_000_000, 0, ok, None, 1, ok)
+    descs = (native.cc_job_desc * 22)(*([big] * 22))
+    assert lib.cc_batch_create(22, descs, None, ctypes.byref(ctx)) == 4
+    opt = native.cc_default_options()
+    opt.sweep_mode = 7
+    descs = (native.cc_job_desc * 1)(good)
+    assert lib.cc_batch_create(1, descs, ctypes.byref(opt), ctypes.byref(ctx)) == 1
+
+
+def test_batch_null_context_calls(native):
+    lib = native.lib
+    out = ctypes.c_int64()
+    n = ctypes.c_int32()
+    assert lib.cc_job_count(None, ctypes.byref(n)) == 1
+    assert lib.cc_job_objective(None, 0, ctypes.byref(out), None) == 1
+    assert lib.cc_job_history(None, 0, 0, None, ctypes.byref(n)) == 1
+    assert lib.cc_job_labels(None, 0, None) == 1
+
+
+def test_python_batch_binding_checks_shapes(native):
+    with pytest.raises(ValueError):
+        native.cc_batch_create([(np.zeros(3, np.int64), np.zeros(0, np.int32), np.zeros(4, np.int32))])
+    with pytest.raises(ValueError):
+        native.cc_batch_create([(np.zeros(3, np.int64), np.zeros(0, np.int32), np.zeros((1, 4), np.int32))])
+
+
+def test_estimate_bytes_host(native):
+    """The footprint estimate is host arithmetic: it grows with every size,
+    counts the creation temporaries on top, and sizes the contingency hash
+    at 2 k n slots (4 k n when every sweep is staged) rounded up to a power
+    of two, 16 bytes a slot."""
+    p1, k1 = native.cc_estimate_bytes([(1000, 20000, 10)])
+    assert k1 > p1 > 0
+    assert native.cc_estimate_bytes([(2000, 20000, 10)])[0] > p1
+    assert native.cc_estimate_bytes([(1000, 40000, 10)])[0] > p1
+    assert native.cc_estimate_bytes([(1000, 20000, 20)])[0] > p1
+    # a batch does not depend on the order of its jobs and holds more than its largest job
+    a = native.cc_estimate_bytes([(1000, 20000, 10), (3000, 50000, 7)])[0]
+    assert a == native.cc_estimate_bytes([(3000, 50000, 7), (1000, 20000, 10)])[0]
+    assert a > native.cc_estimate_bytes([(3000, 50000, 7), (3000, 0, 1)])[0] - native.cc_estimate_bytes([(3000, 0, 1)])[0]
+    # staged-only sweeps double the hash: 2kn + 64 = 20064 -> 32768 slots, 4kn + 64 -> 65536
+    o = native.cc_default_options()
+    o.sweep_mode = 1
+    s1 = native.cc_estimate_bytes([(1000, 20000, 10)], o)[0]
+    assert s1 - p1 == 16 * (65536 - 32768)
+    with pytest.raises(native.CCError):
+        native.cc_estimate_bytes([(0, 0, 3)])
+
+
+def test_server_host_validation(native):
+    lib = native.lib
+    srv = ctypes.c_void_p(7)
+    so = native.cc_server_default_options()
+    assert so.max_active == 4 and so.max_batch_jobs == 256 and so.budget_bytes == 0
+    so.reserved[1] = 3
+    assert lib.cc_server_create(ctypes.byref(so), None, ctypes.byref(srv)) == 1
+    assert srv.value is None
+    so = native.cc_server_default_options()
+    so.max_active = 65
+    assert lib.cc_server_create(ctypes.byref(so), None, ctypes.byref(srv)) == 1
+    so = native.cc_server_default_options()
+    so.budget_bytes = -1
+    assert lib.cc_server_create(ctypes.byref(so), None, ctypes.byref(srv)) == 1
+    o = native.cc_default_options()
+    o.sweep_mode = 5
+    assert lib.cc_server_create(None, ctypes.byref(o), ctypes.byref(srv)) == 1
+    assert lib.cc_server_submit(None, None, None, None) == 1
+    assert lib.cc_server_progress(None, 0, None, 0, None, None) == 1
+    lib.cc_server_destroy(None)

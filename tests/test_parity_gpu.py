@@ -297,7 +297,7 @@ def test_run_timing_and_launch_count(cc):
         sweep_ms, prop_ms = job.last_run_timing()
         assert len(sweep_ms) == len(prop_ms) == done
         assert np.all(sweep_ms > 0) and np.all(prop_ms > 0) and np.all(prop_ms <= sweep_ms)
-        per_sweep = 18 + 3 * 11  # kernels of one unrolled sweep body
+        per_sweep = 19 + 3 * 11  # kernels of one unrolled sweep body
         assert job.launch_count() - base == 1 + ((done + 3) // 4) * 4 * per_sweep
         job.sweep()
         assert len(job.last_run_timing()[0]) == 1

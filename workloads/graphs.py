@@ -20,7 +20,10 @@ def csr_from_edges(n: int, u, v):
     v = np.asarray(v, dtype=np.int64).ravel()
     keep = u != v
     u, v = u[keep], v[keep]
-    key = np.unique(np.concatenate([u * n + v, v * n + u]))
+    key = np.concatenate([u * n + v, v * n + u])
+    key.sort()
+    if len(key):
+        key = key[np.concatenate([[True], key[1:] != key[:-1]])]
     rows = key // n
     cols = (key - rows * n).astype(np.int32)
     counts = np.bincount(rows, minlength=n)
