@@ -1,7 +1,7 @@
 """Benchmark of the consensus sweep on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload lfr|sbm|knn] [--n N] [--k K] [--no-cpu-baseline]
+                    [--workload lfr|sbm|knn|batch|serve] [--n N] [--k K] [--no-cpu-baseline]
 
 One step = one whole consensus job on resident inputs: reset to the singleton
 start (contingency table rebuilt) and synchronous sweeps until no proposal or
@@ -14,6 +14,20 @@ replicas of the job (weak scaling, no collective on the data path).
 
 --impl reference times the CPU oracle (the method written out plainly in C,
 OpenMP over vertices) on the same workload; each step is its first sweep.
+
+--workload batch: the batched form.  4,096 jobs (n log-uniform in
+[200, 200000], half SBM and half LFR-style, k uniform in [5, 64]) drawn from a
+pool of distinct generated jobs, planned into batches by lane bin and device
+budget (cc_plan_batches), each batch one context (cc_batch_create) run to
+convergence; metric jobs/s end to end (host inputs in, labels out), next to
+the same jobs one at a time through cc_create.  Every job's labels are
+compared between the two, and a sample with the oracle.
+
+--workload serve: the served form.  Requests with Poisson arrivals at
+multiples of the one-job-at-a-time service rate, jobs LFR-style (n
+log-uniform in [1000, 2000000], mean degree 10-30, k in [8, 32]) drawn from
+a pool; served by cc_server (continuous batching) and by a one-job-at-a-time
+loop on the same arrivals; p50/p99 latency and jobs/s for each.
 """
 from __future__ import annotations
 
@@ -41,12 +55,20 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["lfr", "sbm", "knn"], default="lfr")
+    p.add_argument("--workload", choices=["lfr", "sbm", "knn", "batch", "serve"], default="lfr")
+    p.add_argument("--jobs", type=int, default=None, help="jobs of the batched / served mix (4096 / 20000)")
+    p.add_argument("--pool", type=int, default=None, help="distinct generated jobs the mix draws from")
+    p.add_argument("--requests", type=int, default=1000, help="served form: requests per arrival rate")
+    p.add_argument("--rates", type=str, default="0.5,0.9,1.5",
+                   help="served form: arrival rates as multiples of the server's saturated jobs/s")
+    p.add_argument("--budget-frac", type=float, default=0.85, help="share of free device memory for batches")
     p.add_argument("--n", type=int, default=None)
     p.add_argument("--k", type=int, default=None)
     p.add_argument("--max-sweeps", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32],
+                   help="lanes per scored item (0 automatic; identical results)")
     p.add_argument("--sweep-mode", type=int, default=0, choices=[0, 1, 2],
                    help="0 automatic, 1 staged deltas, 2 rebuild (identical results)")
     return p.parse_args()
@@ -200,11 +222,269 @@ def cpu_baseline(c):
             "sample": f"whole job: {r.sweeps} synchronous sweeps from the singleton start ({dt:.1f} s)"}, r
 
 
+def mix_pool(args):
+    """Specs of the batched / served mix, the pool job each spec draws, and the pool."""
+    from workloads.configs import batch_job_specs, serve_job_specs
+    from workloads.pool import generate, quantile_pool
+
+    if args.workload == "batch":
+        specs = batch_job_specs(args.jobs or 4096)
+        rep, member = quantile_pool([s[0] for s in specs], args.pool or 256)
+        gen = [(specs[r][0], specs[r][1], specs[r][2], None, specs[r][3]) for r in rep]
+    else:
+        specs = serve_job_specs(args.jobs or 20000)
+        rep, member = quantile_pool([s[0] for s in specs], args.pool or 48)
+        gen = [(specs[r][0], "lfr", specs[r][1], specs[r][2], specs[r][3]) for r in rep]
+    t0 = time.perf_counter()
+    pool = generate(gen)
+    return specs, member, pool, time.perf_counter() - t0
+
+
+def mix_config(args, specs, member, pool, gen_s):
+    ns = np.array([len(pool[m][0]) - 1 for m in member])
+    return {"workload": f"{args.workload}_mix_{len(specs)}", "jobs": len(specs), "pool_distinct_jobs": len(pool),
+            "sum_n": int(ns.sum()), "median_n": float(np.median(ns)),
+            "draw": "specs sorted by n, cut into equal-count groups; each group's middle spec generated once",
+            "generation_s": round(gen_s, 1)}
+
+
+def run_batch(args, rank, world, local, specs, member, pool, gen_s):
+    import torch
+
+    torch.cuda.set_device(local)
+    import paper_2408_11331_gb300 as ccg
+
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    pool = [tuple(pin(a) for a in job) for job in pool]
+    J = len(specs)
+    jobs = [pool[m] for m in member]
+    sizes = [(len(ro) - 1, len(col), lab.shape[0]) for ro, col, lab in jobs]
+    opts = ccg.cc_default_options()
+    budget = int(torch.cuda.mem_get_info()[0] * args.budget_frac)
+    batch_of, nb = ccg._native.cc_plan_batches(sizes, budget, 0, opts)
+    waves = [[] for _ in range(nb)]
+    for j, b in enumerate(batch_of):
+        waves[b].append(j)
+    units = 0.0
+
+    def batched(record=None):
+        nonlocal units
+        dev_ms = 0.0
+        for w in waves:
+            with ccg.ConsensusBatch([jobs[j] for j in w], opts) as b:
+                b.run_until_converged(args.max_sweeps)
+                lab = b.consensus_labels()
+                dev_ms += float(np.sum(b.last_run_timing()[0]))
+                if record is not None:
+                    for i, j in enumerate(w):
+                        record[j] = lab[b.offsets[i]:b.offsets[i + 1]]
+                        units += float(sizes[j][1]) * sizes[j][2] * b.sweeps(i)
+        return dev_ms
+
+    def plain(record=None):
+        for j in range(J):
+            with ccg.Consensus(*jobs[j], opts) as c:
+                c.run_until_converged(args.max_sweeps)
+                lab = c.consensus_labels()
+                if record is not None:
+                    record[j] = lab
+
+    # warm-up: the first batch (code paths, pool of the CUDA allocator)
+    small = waves[0][:64]
+    for _ in range(max(args.warmup, 3)):
+        with ccg.ConsensusBatch([jobs[j] for j in small], opts) as b:
+            b.run_until_converged(args.max_sweeps)
+            b.consensus_labels()
+        with ccg.Consensus(*jobs[small[0]], opts) as c:
+            c.run_until_converged(args.max_sweeps)
+    steps = max(1, args.steps)
+    got = {}
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        dev_ms = 0.0
+        for s_ in range(steps):
+            dev_ms += batched(got if s_ == 0 else None)
+        torch.cuda.synchronize()
+        tb = (time.perf_counter() - t0) / steps
+    ref = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain(ref)
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    same = all(np.array_equal(got[j], ref[j]) for j in range(J))
+    # the oracle on the smallest distinct jobs of the pool
+    import oracle
+
+    by_size = sorted(range(len(pool)), key=lambda i: len(pool[i][0]))[:8]
+    first = {int(m): j for j, m in reversed(list(enumerate(member)))}
+    ok_oracle = True
+    for i in by_size:
+        ro, col, lab = pool[i]
+        r = oracle.sync_run(ro, col, lab, args.max_sweeps)
+        ok_oracle &= bool(np.array_equal(got[first[i]], oracle.renumber(r.C)))
+    cfg = mix_config(args, specs, member, pool, gen_s)
+    cfg.update({"batches": nb, "jobs_per_batch": [len(w) for w in waves], "budget_bytes": budget,
+                "planner": "cc_plan_batches: lane bins of k, then batches within the device budget",
+                "l2": "inputs larger than L2, no flush"})
+    out = {"metric": "batched jobs/s", "value": J / tb, "unit": "jobs/s", "n_gpus": world, "steps": steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
+           "e2e": {"value": J / tb, "unit": "jobs/s", "h2d_bytes_per_step": int(sum(
+               a.nbytes for ro, col, lab in jobs for a in (ro, col, lab))), "d2h_bytes_per_step": int(4 * sum(
+               s_[0] for s_ in sizes))},
+           "device_ms_per_step": dev_ms / steps,
+           "edge_partitions_per_s": units / tb,
+           "plain_loop": {"value": J / tp, "unit": "jobs/s", "ms": 1e3 * tp,
+                          "how": "each job alone: cc_create, run, labels, destroy"},
+           "speedup_vs_plain_loop": tp / tb,
+           "parity": ("bit-exact per job vs one-at-a-time" if same else "MISMATCH") +
+                     ("; oracle sample bit-exact" if ok_oracle else "; oracle sample MISMATCH"),
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args, rank, world, local, specs, member, pool, gen_s):
+    import torch
+
+    torch.cuda.set_device(local)
+    import paper_2408_11331_gb300 as ccg
+    from workloads.configs import poisson_arrivals
+
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    pool = [tuple(pin(a) for a in job) for job in pool]
+    R = min(args.requests, len(member))
+    req = [int(m) for m in member[:R]]
+    opts = ccg.cc_default_options()
+
+    def solo(i):
+        with ccg.Consensus(*pool[i], opts) as c:
+            c.run_until_converged(args.max_sweeps)
+            return c.consensus_labels()
+
+    # reference labels of every pool job, and warm-up
+    ref = {}
+    for i in sorted(set(req)):
+        ref[i] = solo(i)
+    # service rate of the one-job-at-a-time loop
+    probe = req[: min(R, 200)]
+    t0 = time.perf_counter()
+    for i in probe:
+        solo(i)
+    mu = len(probe) / (time.perf_counter() - t0)
+
+    def serve_server(arr):
+        lat = np.zeros(R)
+        with ccg.Server(max_active=8, max_batch_jobs=256, options=opts) as srv:
+            tick = {}
+            nxt = 0
+            bad = 0
+            t0 = time.perf_counter()
+            left = R
+            while left:
+                now = time.perf_counter() - t0
+                while nxt < R and arr[nxt] <= now:
+                    tick[srv.submit(*pool[req[nxt]])] = nxt
+                    nxt += 1
+                done, _ = srv.progress(wait=nxt >= R)
+                now = time.perf_counter() - t0
+                for t in done:
+                    r = tick[t]
+                    lat[r] = now - arr[r]
+                    res = srv.result(t, pop=True)
+                    bad += int(res["status"] != 0 or not np.array_equal(res["labels"], ref[req[r]]))
+                    left -= 1
+            span = time.perf_counter() - t0
+            st = srv.stats()
+        return lat, span, bad, st
+
+    def serve_plain(arr):
+        lat = np.zeros(R)
+        t0 = time.perf_counter()
+        for r in range(R):
+            now = time.perf_counter() - t0
+            if arr[r] > now:
+                time.sleep(arr[r] - now)
+            solo(req[r])
+            lat[r] = time.perf_counter() - t0 - arr[r]
+        return lat, time.perf_counter() - t0
+
+    results = []
+    with Clocks(local) as clk:
+        # saturated throughput of the server: every request waiting at t = 0
+        _, sat_span, sat_bad, _ = serve_server(np.zeros(R))
+        sat = R / sat_span
+        rates = [float(x) * sat for x in args.rates.split(",")]
+        for q, rate in enumerate(rates):
+            arr = poisson_arrivals(R, rate, 0x5EED + 4 + q)
+            lat, span, bad, st = serve_server(arr)
+            plat, pspan = serve_plain(arr)
+            results.append({
+                "rate_jobs_per_s": rate, "rate_vs_saturated": rate / sat,
+                "served": {"jobs_per_s": R / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                           "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mismatches": bad,
+                           "contexts": st["batches"], "max_in_flight": st["max_in_flight"],
+                           "peak_bytes": st["peak_bytes"]},
+                "plain": {"jobs_per_s": R / pspan, "p50_ms": 1e3 * float(np.percentile(plat, 50)),
+                          "p99_ms": 1e3 * float(np.percentile(plat, 99))}})
+    top = results[-1]
+    cfg = mix_config(args, specs, member[:R], pool, gen_s)
+    cfg.update({"requests_per_rate": R, "arrivals": "Poisson, seeds 0x5EED + 4 + rate index",
+                "plain_service_rate_jobs_per_s": mu, "server_saturated_jobs_per_s": sat,
+                "rates": "0.5, 0.9, 1.5 x the server's saturated jobs/s (all requests waiting at t = 0)",
+                "server": "cc_server max_active 8, max_batch_jobs 256"})
+    out = {"metric": "served jobs/s, p50/p99 latency", "value": top["served"]["jobs_per_s"], "unit": "jobs/s",
+           "n_gpus": world, "steps": len(rates), "warmup": 1, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg, "rates": results,
+           "parity": "bit-exact per request vs the job alone" if sat_bad == 0 and all(
+               r["served"]["mismatches"] == 0 for r in results) else "MISMATCH",
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
+def run_mix_reference(args, rank, specs, member, pool, gen_s):
+    """The oracle on the mix's jobs in order, for a bounded time (about 20 s)."""
+    if rank != 0:
+        return
+    import oracle
+
+    t0 = time.perf_counter()
+    done = 0
+    units = 0.0
+    for m in member:
+        ro, col, lab = pool[m]
+        r = oracle.sync_run(ro, col, lab, args.max_sweeps)
+        done += 1
+        units += float(len(col)) * lab.shape[0] * r.sweeps
+        if time.perf_counter() - t0 > 20.0:
+            break
+    dt = time.perf_counter() - t0
+    cfg = mix_config(args, specs, member, pool, gen_s)
+    unit = "jobs/s"
+    out = {"impl": "reference", "metric": "batched jobs/s" if args.workload == "batch" else "served jobs/s, p50/p99 latency",
+           "value": done / dt, "unit": unit, "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * dt,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+           "config": cfg,
+           "cpu_baseline": {"value": done / dt, "unit": unit, "cores": os.cpu_count() or 1, "kind": "oracle",
+                            "sample": f"first {done} jobs of the mix in order, whole runs ({dt:.1f} s)"},
+           "e2e": {"value": done / dt, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload in ("batch", "serve"):
+        if args.impl == "reference" and rank != 0:
+            return
+        specs, member, pool, gen_s = mix_pool(args)
+        if args.impl == "reference":
+            return run_mix_reference(args, rank, specs, member, pool, gen_s)
+        run = run_batch if args.workload == "batch" else run_serve
+        return run(args, rank, world, local, specs, member, pool, gen_s)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -226,6 +506,7 @@ def main():
 
     opts = ccg.cc_default_options()
     opts.sweep_mode = args.sweep_mode
+    opts.lanes = args.lanes
     job = ccg.Consensus(ro, col, lab, opts)
     job.set_stream(stream.cuda_stream)
     for _ in range(max(args.warmup, 3)):
@@ -340,7 +621,8 @@ def main():
                     "h2d_bytes_per_step": int(ro.nbytes + col.nbytes + lab.nbytes),
                     "d2h_bytes_per_step": int(4 * n + 8 * 64),
                     "steps": args.e2e_steps, "ms_per_step": 1e3 * e2e_s / args.e2e_steps},
-            "roofline": {"kernel": "k_propose", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": "proposal step (k_own + k_edges + k_collect, one launch each per sweep)",
+                         "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": peak_src,
                          "algorithmic_bytes_per_step": int(np.sum(balg[:n_sw])),

@@ -73,7 +73,11 @@ typedef struct {
                                deltas); 1 = always
                                staged deltas (the hash is built at the singleton start);
                                2 = always a rebuild */
-    int32_t reserved[3];    /* must be zero */
+    int32_t lanes;          /* lanes of a warp that score one candidate move, one proposal of the
+                               light path or one vertex's own cluster: 1, 2, 4, 8, 16 or 32;
+                               0 = automatic (by the largest k: about 10 partitions per lane).
+                               Results do not depend on it; speed does */
+    int32_t reserved[2];    /* must be zero */
 } cc_options;
 
 /* State of the contingency hash of a context. */
@@ -270,16 +274,30 @@ void cc_destroy(cc_ctx* ctx);
 cc_status cc_estimate_bytes(int32_t jobs, const cc_job_desc* descs, const cc_options* opt, int64_t* persistent,
                             int64_t* peak);
 
+/* Splits jobs into batches for cc_batch_create (host only; the data
+ * pointers are not read): jobs are grouped by lane bin (the k ranges listed
+ * under the served form below) and each group is cut, in job order, into
+ * batches whose peak device bytes (cc_estimate_bytes) fit in budget_bytes
+ * and that hold at most max_jobs jobs (max_jobs <= 0: no limit).
+ * batch_of[j] (int32[jobs], written) receives job j's batch, numbered from 0
+ * in order of lane bin, or -1 for a job that alone needs more than the
+ * budget; *batches receives the number of batches.  Errors: CC_ERR_INVALID,
+ * CC_ERR_OVERFLOW (a job's sizes, as in cc_create). */
+cc_status cc_plan_batches(int32_t jobs, const cc_job_desc* descs, const cc_options* opt, int64_t budget_bytes,
+                          int32_t max_jobs, int32_t* batch_of, int32_t* batches);
+
 /* ---- served form: a request loop with continuous batching ---------------
  * A server takes consensus jobs as they arrive and keeps them resident on
  * the GPU while they run.  Waiting jobs are admitted in arrival order into
  * contexts of many jobs (as cc_batch_create) while a context slot is free and
  * the new context's device bytes (cc_estimate_bytes, peak) fit in what the
  * budget has left; the oldest waiting job opens a context and later ones of
- * the same lane bin (k in the same range: 1..5, 6..10, 11..20, 21..40,
- * 41..80, above 80) join it while they fit.  Every context runs on its
- * own stream, so contexts admitted while others run overlap with them on the
- * device.  A job's results are those of running it alone.  Single-threaded:
+ * the same lane bin (k in the same range: 1..10, 11..20, 21..40, 41..80,
+ * 81..160, above 160) and of similar size (n within a factor 4 of the first
+ * job's) join it while they fit.  Every context runs on its own stream, so
+ * contexts admitted while others run overlap with them on the device;
+ * streams of smaller contexts have higher CUDA priority.  A job's results
+ * are those of running it alone.  Single-threaded:
  * all calls on one server come from one thread at a time.  Device memory
  * comes from a memory pool of the server (stream-ordered allocation). */
 typedef struct cc_server cc_server;
@@ -287,7 +305,7 @@ typedef struct cc_server cc_server;
 typedef struct {
     int64_t budget_bytes;   /* device bytes the server may hold for contexts; 0 = 80% of the
                                free device memory at creation */
-    int32_t max_active;     /* contexts in flight at once (1..64); 0 = 4 */
+    int32_t max_active;     /* contexts in flight at once (1..64); 0 = 8 */
     int32_t max_batch_jobs; /* jobs admitted into one context; 0 = 256 */
     int32_t reserved[4];    /* must be zero */
 } cc_server_options;

@@ -220,9 +220,11 @@ class Server:
             self._live.pop(t, None)
         return done, pending
 
-    def result(self, ticket: int) -> dict:
+    def result(self, ticket: int, pop: bool = False) -> dict:
+        """Labels, objective, sweeps and status of a job; pop=True also drops
+        the labels buffer kept here once the job is done."""
         r = _native.cc_server_job(self._srv, ticket)
-        r["labels"] = self._out[ticket] if r["done"] else None
+        r["labels"] = (self._out.pop(ticket) if pop else self._out[ticket]) if r["done"] else None
         return r
 
     def drain(self):

@@ -24,7 +24,7 @@ EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", 
            "cc_run_until_converged", "cc_last_run_timing", "cc_table_stats", "cc_launch_count", "cc_history", "cc_objective", "cc_objective_recompute",
            "cc_consensus_labels", "cc_cluster_ids", "cc_cluster_ids_dev", "cc_last_error", "cc_destroy",
            "cc_batch_create", "cc_job_count", "cc_job_objective", "cc_job_history", "cc_job_labels",
-           "cc_estimate_bytes", "cc_server_default_options", "cc_server_create", "cc_server_submit",
+           "cc_estimate_bytes", "cc_plan_batches", "cc_server_default_options", "cc_server_create", "cc_server_submit",
            "cc_server_progress", "cc_server_job", "cc_server_stats", "cc_server_last_error", "cc_server_destroy",
            "cc_renumber_noalloc")
 
@@ -41,7 +41,7 @@ class CCError(RuntimeError):
 class cc_options(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("table_log2", ctypes.c_int32), ("table_start_log2", ctypes.c_int32),
-                ("sweep_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("sweep_mode", ctypes.c_int32), ("lanes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class cc_table_info(ctypes.Structure):
@@ -138,6 +138,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cc_estimate_bytes.restype = c.c_int
     lib.cc_estimate_bytes.argtypes = [c.c_int32, c.POINTER(cc_job_desc), c.POINTER(cc_options),
                                       c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
+    lib.cc_plan_batches.restype = c.c_int
+    lib.cc_plan_batches.argtypes = [c.c_int32, c.POINTER(cc_job_desc), c.POINTER(cc_options), c.c_int64, c.c_int32,
+                                    P, c.POINTER(c.c_int32)]
     lib.cc_server_default_options.restype = None
     lib.cc_server_default_options.argtypes = [c.POINTER(cc_server_options)]
     lib.cc_server_create.restype = c.c_int
@@ -384,6 +387,18 @@ def cc_estimate_bytes(sizes, options: cc_options | None = None):
     _check(lib.cc_estimate_bytes(len(sizes), descs, ctypes.byref(options) if options is not None else None,
                                  ctypes.byref(a), ctypes.byref(b)), None)
     return a.value, b.value
+
+
+def cc_plan_batches(sizes, budget_bytes: int, max_jobs: int = 0, options: cc_options | None = None):
+    """sizes: sequence of (n, nnz, k) -> (batch index of every job (-1: over the budget), number of batches)."""
+    descs = (cc_job_desc * max(len(sizes), 1))()
+    for j, (n, nnz, k) in enumerate(sizes):
+        descs[j] = cc_job_desc(n, nnz, None, None, k, None)
+    out = np.empty(max(len(sizes), 1), np.int32)
+    nb = ctypes.c_int32(0)
+    _check(lib.cc_plan_batches(len(sizes), descs, ctypes.byref(options) if options is not None else None,
+                               budget_bytes, max_jobs, _ptr(out), ctypes.byref(nb)), None)
+    return out[: len(sizes)], nb.value
 
 
 def _check_server(status: int, srv=None):

@@ -346,6 +346,8 @@ cc_status check_options(const cc_options& opt, std::string* msg)
     if (opt.table_log2 < 0 || opt.table_log2 > 40) return bad(CC_ERR_INVALID, "table_log2 out of range");
     if (opt.table_start_log2 < 0 || opt.table_start_log2 > 40) return bad(CC_ERR_INVALID, "table_start_log2 out of range");
     if (opt.sweep_mode < 0 || opt.sweep_mode > 2) return bad(CC_ERR_INVALID, "sweep_mode must be 0, 1 or 2");
+    if (opt.lanes < 0 || opt.lanes > 32 || (opt.lanes & (opt.lanes - 1)) != 0)
+        return bad(CC_ERR_INVALID, "lanes must be 0 or a power of two up to 32");
     return CC_OK;
 }
 
@@ -368,7 +370,7 @@ void finish_plan(Plan& p, const cc_options& opt)
     const size_t N = (size_t)p.n, J = (size_t)jobs;
     const size_t per[] = {
         sizeof(JobInfo) * J, sizeof(JobState) * J, 8 * (N + 1), 4 * (size_t)p.nnz, 4 * (size_t)p.nnz,
-        4 * N, 4 * (size_t)p.rows, 16 * (size_t)p.rows, 4 * N, 4 * N, 4 * N, 8 * N, 4 * N,
+        4 * N, 4 * (size_t)p.rows, 8 * (size_t)p.rows, 4 * N, 4 * N, 4 * N, 8 * N, 4 * N,
         sizeof(Slot) * (size_t)p.cap_max, 4 * N, 4 * N, 4 * N, 4 * N, N, 4 * N, 4 * N, 4 * (N / 1024 + 2),
         4 * (3 * N + N / 1024 + 64), sizeof(DevState), sizeof(cc_sweep_info) * J * (size_t)p.hist_cap};
     for (size_t b : per) p.persistent += rounded(b);
@@ -382,7 +384,7 @@ void finish_plan(Plan& p, const cc_options& opt)
 namespace {
 
 cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_options* opt_in, void* stream,
-                        cudaMemPool_t pool, cc_ctx** out)
+                        cudaMemPool_t pool, cc_ctx** out, int priority = 0)
 {
     if (!out) return fail(nullptr, CC_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -423,7 +425,7 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
 
     CC_TRY(cudaGetDevice(&c->device));
     CC_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
-    CC_TRY(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    CC_TRY(cudaStreamCreateWithPriority(&c->own_stream, cudaStreamNonBlocking, priority));
     // pooled memory is allocated in the order of the context's own stream, so
     // such a context runs on that stream
     c->stream = (stream && !pool) ? static_cast<cudaStream_t>(stream) : c->own_stream;
@@ -613,6 +615,7 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     a.cap_min = cap < 1024 ? cap : 1024;
     a.keys = (unsigned long long)keys;
     a.sweep_mode = c->opt.sweep_mode;
+    a.gs = c->opt.lanes > 0 ? c->opt.lanes : lanes_for_k(kmax);
     a.pv = c->pv;
     a.pa = c->pa;
     a.pb = c->pb;
@@ -775,9 +778,9 @@ cc_status launch_chunk(cc_ctx* c)
 namespace ccg {
 
 cc_status ctx_create(int jobs, const JobInput* in, bool on_device, const cc_options* opt, void* stream,
-                     cudaMemPool_t pool, cc_ctx** out)
+                     cudaMemPool_t pool, cc_ctx** out, int priority)
 {
-    return create_common(jobs, in, on_device, opt, stream, pool, out);
+    return create_common(jobs, in, on_device, opt, stream, pool, out, priority);
 }
 
 cc_status ctx_async_start(cc_ctx* c, int limit, DevState* pinned)

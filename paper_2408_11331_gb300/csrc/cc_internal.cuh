@@ -17,11 +17,10 @@
 //                      g = (i << s_j) | rep, rep the job-local index of the least vertex
 //                      carrying that label in partition i and 2^s_j >= n_j, so g names
 //                      (partition, label) within the job and g < 2 k_j n_j.
-//   summ  int4[...]    same layout as G, one row per cluster id: per partition i
-//                      {d, m, m2, 0}: d the label id that was most frequent in the
-//                      cluster at the last table rebuild, m the exact current count of
-//                      d (kept by every commit), m2 an upper bound on the count of any
-//                      other label of partition i in the cluster.
+//   summ  int2[...]    same layout as G, one row per cluster id: per partition i
+//                      {d, m}: d the label id that was most frequent in the cluster at
+//                      the last table rebuild, m the exact current count of d (kept by
+//                      every commit); |cluster| - m bounds the count of any other label.
 //   C     int32[N]     cluster id of each vertex
 //   size  int32[N]     cluster sizes, indexed by cluster id
 //   table Slot[cap]    the contingency counts n(c, i, l) of all jobs as one open-
@@ -117,7 +116,7 @@ struct SweepArgs {
     const JobInfo* job;         // J
     JobState* js;               // J
     const int* G;
-    int4* summ;
+    int2* summ;
     int* C;
     int* size;
     int* dsize;                 // staged size deltas
@@ -128,6 +127,7 @@ struct SweepArgs {
     unsigned long long cap_min;  // smallest active capacity
     unsigned long long keys;     // sum_j k_j n_j: no C has more live keys
     int sweep_mode;              // 0 automatic, 1 always staged deltas, 2 always rebuild
+    int gs;                      // lanes that score one item (a power of two, 1..32)
     int* pv;                    // proposal list: vertex,
     int* pa;                    //   source cluster,
     int* pb;                    //   target cluster,
@@ -178,16 +178,14 @@ __device__ __forceinline__ unsigned long long ckey(int c, int g)
     return ((unsigned long long)(unsigned)c << 32) | (unsigned)g;
 }
 
-// Keeps the summary row of the slot's (cluster, partition) valid after its
-// count changed by d to newc: the count of the row's label is exact, the
-// bound on the other labels only rises.
-__device__ __forceinline__ void summ_update(const SweepArgs& a, unsigned long long key, int d, int newc)
+// Keeps the summary row of the slot's (cluster, partition) exact after its
+// count changed by d: only the count of the row's own label is stored.
+__device__ __forceinline__ void summ_update(const SweepArgs& a, unsigned long long key, int d)
 {
     const int x = (int)(key >> 32), g = (int)(unsigned)(key & 0xffffffffull);
     const JobInfo& J = a.job[a.jid[x]];
-    int4* S = a.summ + row_of(J, x) + (g >> J.lshift);
+    int2* S = a.summ + row_of(J, x) + (g >> J.lshift);
     if (S->x == g) atomicAdd(&S->y, d);
-    else if (d > 0) atomicMax(&S->z, newc);
 }
 
 __device__ __forceinline__ void set_err(DevState* st, int code)
@@ -396,7 +394,7 @@ void set_thread_error(const std::string& msg);
 cudaError_t launch_run_begin(const SweepArgs& a, int limit, cudaStream_t s);
 // One sweep of every job; prop0/prop1 (may be null) are recorded around the
 // proposal kernels.
-constexpr int kKernelsPerRebuild = 11;
+constexpr int kKernelsPerRebuild = 8;
 constexpr int kKernelsPerSweep = 19 + 3 * kKernelsPerRebuild;
 cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaEvent_t prop0,
                          cudaEvent_t prop1);

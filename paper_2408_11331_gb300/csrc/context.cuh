@@ -34,7 +34,7 @@ struct cc_ctx {
     int* src = nullptr;
     int* jid = nullptr;
     int* G = nullptr;
-    int4* summ = nullptr;
+    int2* summ = nullptr;
     int* C = nullptr;
     int* size = nullptr;
     int* dsize = nullptr;
@@ -108,9 +108,10 @@ int lanes_for_k(int k);
 cc_options resolve_options(const cc_options* opt);
 
 // cc_create / cc_batch_create with device memory from `pool` (stream-ordered
-// allocation on the context's own stream) when pool is not null.
+// allocation on the context's own stream) when pool is not null; the own
+// stream gets the given CUDA stream priority (lower numbers run first).
 cc_status ctx_create(int jobs, const JobInput* in, bool on_device, const cc_options* opt, void* stream,
-                     cudaMemPool_t pool, cc_ctx** out);
+                     cudaMemPool_t pool, cc_ctx** out, int priority = 0);
 
 // Starts a run of at most `limit` sweeps without waiting: queues the run and
 // its first graph launch, then a copy of the control block into `pinned` and

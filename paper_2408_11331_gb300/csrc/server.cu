@@ -12,10 +12,14 @@
 //      anything is allocated) fit in what the budget has left.  The oldest
 //      waiting job opens the new context; later waiting jobs join it in
 //      arrival order if they fall in the same lane bin (the number of lanes
-//      that score one move, set by k) and still fit.  The jobs of a context
+//      that score one move, set by k), have a size within a factor 4 of the
+//      first job's n (a context finishes with its slowest job, so a small job
+//      does not wait for a large one) and still fit.  The jobs of a context
 //      run as one disjoint union in the same kernel launches, on the
 //      context's own stream, so contexts admitted while others run overlap
-//      with them on the device.
+//      with them on the device.  Streams of smaller contexts get a higher
+//      priority: when contexts share the GPU, the thread blocks of short jobs
+//      are scheduled first, which keeps their latency close to running alone.
 // Every job's results are those of running it alone (the sweep of a union is
 // per-job exact), so results do not depend on the mix it was served in.
 #include <algorithm>
@@ -70,6 +74,7 @@ struct cc_server {
     std::deque<int64_t> finished;  // done, not yet reported by progress
     int64_t next_ticket = 0;
     size_t in_use = 0;
+    int prio_least = 0, prio_greatest = 0;  // CUDA stream priority range (greatest is the lowest number)
     cc_server_info info{};
     std::string err;
 };
@@ -177,6 +182,17 @@ int poll_flights(cc_server* s)
     return finished;
 }
 
+// Stream priority of a context with the given work size (label rows plus CSR
+// entries): the device's greatest priority up to 2^16, then one step lower
+// per factor 8, down to its least priority.
+int priority_for(const cc_server* s, double work)
+{
+    int level = 0;
+    for (double w = 65536.0; w < work; w *= 8.0) ++level;
+    const int p = s->prio_greatest + level;
+    return p > s->prio_least ? s->prio_least : p;
+}
+
 // Admits waiting jobs into new contexts; returns how many jobs were admitted.
 int admit(cc_server* s)
 {
@@ -198,6 +214,7 @@ int admit(cc_server* s)
         for (size_t q = 1; q < look && (int)take.size() < s->sopt.max_batch_jobs; ++q) {
             const ServerJob& j = s->queue[q];
             if (j.bin != first.bin) continue;
+            if ((long long)j.in.n > 4LL * first.in.n || 4LL * j.in.n < (long long)first.in.n) continue;
             Plan t = acc;
             add_totals(t, job_totals(j.in));
             if (t.n >= (1LL << 31) || s->in_use + peak_bytes(t, s->opt) > budget) continue;
@@ -215,7 +232,8 @@ int admit(cc_server* s)
         finish_plan(p, s->opt);
         f.bytes = p.persistent;
         f.slot = s->free_slots.back();
-        cc_status st = ctx_create((int)in.size(), in.data(), false, &s->opt, nullptr, s->pool, &f.ctx);
+        cc_status st = ctx_create((int)in.size(), in.data(), false, &s->opt, nullptr, s->pool, &f.ctx,
+                                  priority_for(s, (double)acc.keys + (double)acc.nnz));
         if (st == CC_OK) st = ctx_async_start(f.ctx, s->opt.max_sweeps, s->pinned + f.slot);
         if (st != CC_OK) {
             s->err = f.ctx ? cc_last_error(f.ctx) : cc_last_error(nullptr);
@@ -239,11 +257,61 @@ int admit(cc_server* s)
 
 extern "C" {
 
+cc_status cc_plan_batches(int32_t jobs, const cc_job_desc* descs, const cc_options* opt, int64_t budget_bytes,
+                          int32_t max_jobs, int32_t* batch_of, int32_t* batches)
+{
+    if (jobs < 1 || !descs || !batch_of || budget_bytes <= 0)
+        return sfail(nullptr, CC_ERR_INVALID, "cc_plan_batches needs jobs >= 1, descriptors, output and a budget");
+    const cc_options o = resolve_options(opt);
+    std::string msg;
+    cc_status r = check_options(o, &msg);
+    if (r != CC_OK) return sfail(nullptr, r, msg);
+    std::vector<JobInput> in(jobs);
+    for (int j = 0; j < jobs; ++j) {
+        in[j] = JobInput{descs[j].n, descs[j].nnz, descs[j].row_off, descs[j].col, descs[j].k, descs[j].labels};
+        Plan p;
+        r = plan_jobs(1, &in[j], o, &p, &msg);
+        if (r != CC_OK) return sfail(nullptr, r, "job " + std::to_string(j) + ": " + msg);
+    }
+    // lane bins in increasing order, jobs in index order within a bin
+    std::vector<int> order(jobs);
+    for (int j = 0; j < jobs; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return lanes_for_k(in[x].k) < lanes_for_k(in[y].k); });
+    const size_t budget = (size_t)budget_bytes;
+    int nb = 0, open_bin = -1, count = 0;
+    Plan acc;
+    for (int j : order) {
+        const Plan one = job_totals(in[j]);
+        if (peak_bytes(one, o) > budget) {
+            batch_of[j] = -1;
+            continue;
+        }
+        const int bin = lanes_for_k(in[j].k);
+        Plan t = acc;
+        add_totals(t, one);
+        const bool fits = open_bin == bin && (max_jobs <= 0 || count < max_jobs) && t.n < (1LL << 31) &&
+                          peak_bytes(t, o) <= budget;
+        if (!fits) {
+            ++nb;
+            open_bin = bin;
+            count = 0;
+            acc = one;
+        } else {
+            acc = t;
+        }
+        batch_of[j] = nb - 1;
+        ++count;
+    }
+    if (batches) *batches = nb;
+    return CC_OK;
+}
+
 void cc_server_default_options(cc_server_options* o)
 {
     if (!o) return;
     *o = cc_server_options{};
-    o->max_active = 4;
+    o->max_active = 8;
     o->max_batch_jobs = 256;
 }
 
@@ -258,7 +326,7 @@ cc_status cc_server_create(const cc_server_options* sopt, const cc_options* opt,
         if (r != 0) return sfail(nullptr, CC_ERR_INVALID, "reserved server option fields must be zero");
     if (so.budget_bytes < 0 || so.max_active < 0 || so.max_batch_jobs < 0)
         return sfail(nullptr, CC_ERR_INVALID, "server options must not be negative");
-    if (so.max_active == 0) so.max_active = 4;
+    if (so.max_active == 0) so.max_active = 8;
     if (so.max_active > 64) return sfail(nullptr, CC_ERR_INVALID, "max_active must be <= 64");
     if (so.max_batch_jobs == 0) so.max_batch_jobs = 256;
     const cc_options o = resolve_options(opt);
@@ -276,6 +344,8 @@ cc_status cc_server_create(const cc_server_options* sopt, const cc_options* opt,
     };
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) return bail(e, "cudaGetDevice");
+    e = cudaDeviceGetStreamPriorityRange(&s->prio_least, &s->prio_greatest);
+    if (e != cudaSuccess) return bail(e, "cudaDeviceGetStreamPriorityRange");
     if (so.budget_bytes == 0) {
         size_t free_b = 0, total_b = 0;
         e = cudaMemGetInfo(&free_b, &total_b);

@@ -3,6 +3,7 @@
 // label compaction into the vertex-major membership matrix, the singleton
 // state, the contingency hash rebuild with its summary rows, and the
 // from-scratch objective used for checks.
+#include <algorithm>
 #include <climits>
 
 #include "cc_internal.cuh"
@@ -210,7 +211,7 @@ __global__ void k_summ_singletons(SweepArgs a, long long rows)
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
         const int g = a.G[r];
-        a.summ[r] = g >= 0 ? make_int4(g, 1, 0, 0) : make_int4(-1, 0, 0, 0);
+        a.summ[r] = g >= 0 ? make_int2(g, 1) : make_int2(-1, 0);
     }
 }
 
@@ -251,25 +252,22 @@ __device__ __forceinline__ bool rebuild_off(const DevState* st, int conditional)
     return conditional && (!st->rebuild || st->err);
 }
 
-// Clears the slots of the capacity being built (st->new_mask + 1 of them), and
-// the staged size deltas after an abandoned sweep.
-__global__ void k_table_clear(SweepArgs a, int conditional)
+// Clears the slots of the capacity being built (st->new_mask + 1 of them),
+// the summary rows, the occupied-slot counter, and the staged size deltas
+// after an abandoned sweep.
+__global__ void k_table_clear(SweepArgs a, long long rows, int conditional)
 {
-    const DevState* st = a.st;
+    DevState* st = a.st;
     if (rebuild_off(st, conditional)) return;
     const unsigned long long cap = st->new_mask + 1;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (unsigned long long s = t0; s < cap; s += stride)
         reinterpret_cast<ulonglong2*>(a.table)[s] = make_ulonglong2(kEmpty, 0ull);
+    for (unsigned long long r = t0; r < (unsigned long long)rows; r += stride) a.summ[r] = make_int2(0, 0);
     if (st->abort)
         for (unsigned long long v = t0; v < (unsigned long long)a.n; v += stride) a.dsize[v] = 0;
-}
-
-__global__ void k_table_reset_counters(DevState* st, int conditional)
-{
-    if (rebuild_off(st, conditional)) return;
-    st->used = 0;
+    if (t0 == 0) st->used = 0;
 }
 
 __device__ __forceinline__ int warp_incl_scan(int x, int lane)
@@ -355,9 +353,13 @@ __global__ void k_table_build(SweepArgs a, int conditional)
 {
     DevState* st = a.st;
     if (rebuild_off(st, conditional)) return;
+    __shared__ unsigned long long s_used;
+    if (threadIdx.x == 0) s_used = 0;
+    __syncthreads();
     const unsigned long long mask = st->new_mask;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
+    unsigned long long used = 0;  // slots this warp created (lane 0 counts)
     for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += stride) {
         const long long m = base + threadIdx.x;
         const bool valid = m < a.n;
@@ -380,25 +382,19 @@ __global__ void k_table_build(SweepArgs a, int conditional)
                 if (s < 0) set_err(st, CC_ERR_TABLE_FULL);
                 else atomicAdd(&a.table[s].cnt, __popc(same));
             }
-            const unsigned mi = __ballot_sync(0xffffffffu, ins);
-            if (lane == 0 && mi) atomicAdd(&st->used, (unsigned long long)__popc(mi));
+            used += __popc(__ballot_sync(0xffffffffu, ins));
         }
     }
+    // one add per block: st->used is a single word that every block updates
+    if (lane == 0 && used) atomicAdd(&s_used, used);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_used) atomicAdd(&st->used, s_used);
 }
 
-// Summary rows of the rebuilt table.  The first 8 bytes of a row entry are
-// read as one unsigned 64-bit value (count << 32 | label id), so an atomic
-// maximum over the slots of a (cluster, partition) leaves the most frequent
-// label and its count (ties to the larger id); a second pass takes the largest
-// count of the other labels.
-__global__ void k_summ_clear(SweepArgs a, long long rows, int conditional)
-{
-    if (rebuild_off(a.st, conditional)) return;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride)
-        a.summ[r] = make_int4(0, 0, 0, 0);
-}
-
+// Summary rows of the rebuilt table.  A row entry is read as one unsigned
+// 64-bit value (count << 32 | label id), so an atomic maximum over the slots
+// of a (cluster, partition) leaves the most frequent label and its count
+// (ties to the larger id).
 // With eval set (the first rebuild of a heavy sweep) this pass also adds
 // -2 sum n^2 over the new keys to each job's recompute (the table part of F').
 __global__ void k_summ_top(SweepArgs a, int conditional, int eval)
@@ -422,23 +418,6 @@ __global__ void k_summ_top(SweepArgs a, int conditional, int eval)
         if (ev) acc.add(job, -2LL * cnt * cnt);
     }
     if (ev) job_acc_finish(acc, a.jobs);
-}
-
-__global__ void k_summ_second(SweepArgs a, int conditional)
-{
-    const DevState* st = a.st;
-    if (rebuild_off(st, conditional)) return;
-    const unsigned long long cap = st->new_mask + 1;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += stride) {
-        const ulonglong2 e = reinterpret_cast<const ulonglong2*>(a.table)[s];
-        const int cnt = (int)(unsigned)(e.y & 0xffffffffull);
-        if (e.x == kEmpty || cnt <= 0) continue;
-        const int x = (int)(e.x >> 32), g = (int)(unsigned)(e.x & 0xffffffffull);
-        const JobInfo& J = a.job[a.jid[x]];
-        int4* S = a.summ + row_of(J, x) + (g >> J.lshift);
-        if (S->x != g) atomicMax(&S->z, cnt);
-    }
 }
 
 __global__ void k_table_done(DevState* st, int conditional)
@@ -534,17 +513,14 @@ cudaError_t launch_table_rebuild(const SweepArgs& a, long long rows, bool condit
 {
     const int c = conditional ? 1 : 0;
     const int nb = (int)((a.n + 1023) / 1024);
-    k_table_clear<<<grid_for((long long)a.mask_max + 1), kSetupBlock, 0, s>>>(a, c);
-    k_table_reset_counters<<<1, 1, 0, s>>>(a.st, c);
+    k_table_clear<<<grid_for(std::max((long long)a.mask_max + 1, rows)), kSetupBlock, 0, s>>>(a, rows, c);
     k_scan_blocks<<<nb, 1024, 0, s>>>(a, c);
     k_scan_sums<<<1, 1024, 0, s>>>(a, nb, c);
     k_scan_write<<<nb, 1024, 0, s>>>(a, c);
     k_members_scatter<<<grid_for(a.n), kSetupBlock, 0, s>>>(a, c);
     k_table_build<<<grid_for(a.n), kSetupBlock, 0, s>>>(a, c);
-    k_summ_clear<<<grid_for(rows), kSetupBlock, 0, s>>>(a, rows, c);
     k_summ_top<<<grid_for((long long)a.mask_max + 1), kSetupBlock, eval ? smem_jobs_bytes(a.jobs) : 0, s>>>(a, c,
                                                                                                  eval ? 1 : 0);
-    k_summ_second<<<grid_for((long long)a.mask_max + 1), kSetupBlock, 0, s>>>(a, c);
     k_table_done<<<1, 1, 0, s>>>(a.st, c);
     return cudaGetLastError();
 }

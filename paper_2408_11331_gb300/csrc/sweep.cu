@@ -117,23 +117,24 @@ __device__ __forceinline__ int group_sum(int x, int gs)
     return x;
 }
 
-// Summary part of A_x(v) for a non-singleton cluster x of job J, lanes of a
-// group over the partitions i = l, l + gs, ...: ex = sum of m where v carries
-// the row's label d (exact there), ub = ex + sum of m2 elsewhere (an upper
-// bound on A_x).
+// Summary part of A_x(v) for a non-singleton cluster x (size sx) of job J,
+// lanes of a group over the partitions i = l, l + gs, ...: ex = sum of m where
+// v carries the row's label d (exact there), ub = ex + sum of (sx - m)
+// elsewhere: the members not carrying d bound the count of any other label,
+// so ub is an upper bound on A_x.
 __device__ __forceinline__ void summary_part(const SweepArgs& a, const JobInfo& J, const int* __restrict__ gv, int x,
-                                             int l, int gs, int& ex, int& ub)
+                                             int sx, int l, int gs, int& ex, int& ub)
 {
     ex = 0;
     ub = 0;
-    const int4* S = a.summ + row_of(J, x);
+    const int2* S = a.summ + row_of(J, x);
     for (int i0 = l; i0 < J.k; i0 += gs * kInflight) {
-        int4 r[kInflight];
+        int2 r[kInflight];
         int g[kInflight];
 #pragma unroll
         for (int b = 0; b < kInflight; ++b) {
             const int i = i0 + b * gs;
-            r[b] = make_int4(-1, 0, 0, 0);
+            r[b] = make_int2(-1, 0);
             g[b] = -2;
             if (i < J.k) {
                 r[b] = __ldg(S + i);
@@ -145,18 +146,20 @@ __device__ __forceinline__ void summary_part(const SweepArgs& a, const JobInfo& 
             if (i0 + b * gs < J.k) {
                 const bool eq = g[b] == r[b].x;
                 ex += eq ? r[b].y : 0;
-                ub += eq ? r[b].y : r[b].z;
+                ub += eq ? r[b].y : sx - r[b].y;
             }
         }
     }
 }
 
 // Exact counts of the partitions the summary leaves open (v does not carry
-// the row's label and another label may be present), by hash probes.
+// the row's label and some member of x does not carry it either), by hash
+// probes.
 __device__ __forceinline__ int probe_part(const SweepArgs& a, const JobInfo& J, const Slot* __restrict__ table,
-                                          unsigned long long mask, const int* __restrict__ gv, int x, int l, int gs)
+                                          unsigned long long mask, const int* __restrict__ gv, int x, int sx, int l,
+                                          int gs)
 {
-    const int4* S = a.summ + row_of(J, x);
+    const int2* S = a.summ + row_of(J, x);
     int acc = 0;
     for (int i0 = l; i0 < J.k; i0 += gs * kInflight) {
         unsigned long long key[kInflight], h[kInflight];
@@ -170,9 +173,9 @@ __device__ __forceinline__ int probe_part(const SweepArgs& a, const JobInfo& J, 
             h[b] = 0;
             ev[b] = make_ulonglong2(kEmpty, 0ull);
             if (i < J.k) {
-                const int4 r = __ldg(S + i);
+                const int2 r = __ldg(S + i);
                 const int g = __ldg(gv + i);
-                on[b] = g != r.x && r.z > 0;
+                on[b] = g != r.x && sx > r.y;
                 if (on[b]) {
                     key[b] = ckey(x, g);
                     h[b] = hash_key(key[b]) & mask;
@@ -213,12 +216,14 @@ __device__ __forceinline__ int row_part(const int* gu_row, const int* gv_row, in
     return acc;  // includes the kp - k padding entries (-1 in every row)
 }
 
-// Lanes per vertex (k_own) or per edge (k_edges): about five partitions per
-// lane for the largest k of the context.
+// Automatic lanes per scored item (vertex, candidate or proposal): about ten
+// partitions per lane for the largest k of the context.  Fewer lanes per item
+// means more items per warp and fewer group reductions; timed on GB300 over
+// 1..32 lanes, this was fastest for k = 20 (2 lanes) and k = 50 (8 lanes).
 __host__ __device__ __forceinline__ int lanes_per_item(int k)
 {
     int gs = 1;
-    while (gs < 32 && gs * 5 < k) gs <<= 1;
+    while (gs < 32 && gs * 10 < k) gs <<= 1;
     return gs;
 }
 
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
     DevState* st = a.st;
     if (st->skip) return;
     const unsigned long long mask = st->mask;
-    const int gs = lanes_per_item(a.kmax);
+    const int gs = a.gs;
     const int lane = threadIdx.x & 31, l = lane & (gs - 1);
     const long long groups = (long long)gridDim.x * blockDim.x / gs;
     const JobInfo J0 = a.job[0];
@@ -242,15 +247,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
         const long long v = base + lane / gs;
         const bool valid = v < a.n;
         const int j = (kSingle || !valid) ? 0 : __ldg(a.jid + v);
-        const JobInfo J = kSingle ? J0 : a.job[j];
         const bool on = valid && (kSingle || !a.js[j].stop);
+        if (!kSingle && !__any_sync(kFull, on)) continue;  // vertices of stopped jobs only
+        const JobInfo J = kSingle ? J0 : a.job[j];
         const int cv = on ? __ldg(a.C + v) : 0;
         const int sa = on ? __ldg(a.size + cv) : 1;
         const int* gv = a.G + row_of(J, on ? v : J.vo);
         int ex = 0, ub = 0, pb = 0;
         if (sa > 1) {
-            summary_part(a, J, gv, cv, l, gs, ex, ub);
-            pb = probe_part(a, J, a.table, mask, gv, cv, l, gs);
+            summary_part(a, J, gv, cv, sa, l, gs, ex, ub);
+            pb = probe_part(a, J, a.table, mask, gv, cv, sa, l, gs);
         }
         const int A = group_sum(ex + pb, gs);
         if (on && l == 0) a.aown[v] = sa > 1 ? A : J.k;
@@ -264,7 +270,8 @@ struct EdgeScratch {
 
 // CSR entries 32 at a time per warp: each lane reads one entry (v, u) and
 // keeps it if v's job runs and u lies in another cluster than v (self-loops
-// and repeats of the same (v, C[u]) inside the warp are dropped); the kept
+// and repeats of the same (v, C[u]) inside the warp are dropped, and so is a
+// candidate whose gain is >= 0 even with A_x at its bound k |x|); the kept
 // entries are then scored by groups of lanes.  A singleton {u} is scored from
 // the two label rows; another cluster from its summary rows, then (unless the
 // lower bound on dD from the summary is already >= 0, in which case the move
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
     if (st->skip) return;
     __shared__ EdgeScratch sh[kWarpsPerBlock];
     const unsigned long long mask = st->mask;
-    const int gs = lanes_per_item(a.kmax), per = 32 / gs;
+    const int gs = a.gs, per = 32 / gs;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, l = lane & (gs - 1);
     const unsigned lt = (1u << lane) - 1u;
     EdgeScratch& es = sh[w];
@@ -287,30 +294,44 @@ __global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
     const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
     for (long long base = ((long long)blockIdx.x * kWarpsPerBlock + w) * 32; base < a.nnz; base += nwarps * 32) {
         const long long e = base + lane;
-        int v = 0, u = 0, x = -1, j = 0;
+        int v = 0, u = 0, x = -1, j = 0, cv = 0;
         if (e < a.nnz) {
             v = __ldg(a.src + e);
             if (!kSingle) j = __ldg(a.jid + v);
+        }
+        // a chunk whose entries all belong to stopped jobs is skipped whole
+        if (!kSingle && __all_sync(kFull, e >= a.nnz || a.js[j].stop)) continue;
+        if (e < a.nnz) {
             u = __ldg(a.col + e);
             if (u != v && (kSingle || !a.js[j].stop)) {
                 x = __ldg(a.C + u);
-                if (x == __ldg(a.C + v)) x = -1;
+                cv = __ldg(a.C + v);
+                if (x == cv) x = -1;
             }
         }
         const unsigned long long pair = x >= 0 ? ((unsigned long long)(unsigned)v << 32) | (unsigned)x : kEmpty;
         const unsigned same = __match_any_sync(kFull, pair);
-        const bool keep = x >= 0 && (__ffs(same) - 1) == lane;
+        bool keep = x >= 0 && (__ffs(same) - 1) == lane;
+        int sx = 0, sa = 0, Aa = 0;
+        if (keep) {
+            sx = __ldg(a.size + x);
+            sa = __ldg(a.size + cv);
+            Aa = __ldg(a.aown + v);
+            // exact prune: n(x, i, l) <= |x| gives A_x <= k |x|, so a move whose
+            // gain is >= 0 even at that bound is never proposed
+            const long long k = kSingle ? J0.k : a.job[j].k;
+            if (2 * ((long long)Aa - k - k * sx) - k * ((long long)sa - 1 - sx) >= 0) keep = false;
+        }
         const unsigned km = __ballot_sync(kFull, keep);
         if (keep) {
             const int p = __popc(km & lt);
-            const int cv = __ldg(a.C + v);
             es.v[p] = v;
             es.u[p] = u;
             es.x[p] = x;
             if (!kSingle) es.j[p] = j;
-            es.sx[p] = __ldg(a.size + x);
-            es.sa[p] = __ldg(a.size + cv);
-            es.Aa[p] = __ldg(a.aown + v);
+            es.sx[p] = sx;
+            es.sa[p] = sa;
+            es.Aa[p] = Aa;
         }
         __syncwarp();
         const int nf = __popc(km);
@@ -326,13 +347,13 @@ __global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
             const int* gv = a.G + row_of(J, valid ? ev : J.vo);
             int rc = 0, ex = 0, ub = 0;
             if (single) rc = row_part(a.G + row_of(J, eu), gv, J.kp >> 2, l, gs);
-            if (table) summary_part(a, J, gv, ex_, l, gs, ex, ub);
+            if (table) summary_part(a, J, gv, ex_, sx, l, gs, ex, ub);
             rc = group_sum(rc, gs);
             ex = group_sum(ex, gs);
             ub = group_sum(ub, gs);
             const bool open = table && 2 * (Aa - k - ub) - k * (sa - 1 - sx) < 0;
             int pb = 0;
-            if (open) pb = probe_part(a, J, a.table, mask, gv, ex_, l, gs);
+            if (open) pb = probe_part(a, J, a.table, mask, gv, ex_, sx, l, gs);
             pb = group_sum(pb, gs);
             if ((single || open) && l == 0) {
                 const int A = single ? rc - (J.kp - k) : ex + pb;
@@ -534,10 +555,26 @@ __device__ __forceinline__ void count_inserts(DevState* st, int mine, unsigned l
     }
 }
 
-// Thread per proposal, over its job's partitions.  Staging never fails: if
-// the table runs short of slots the sweep is abandoned (st->overflow) before
-// anything is committed, and the sweep end schedules a larger table and a
-// retry.
+// The light-path kernels give each proposal a group of gs lanes: the lanes
+// split the job's partitions, and the group's first lane does the per-proposal
+// work (flags, sizes, bids, sums).  Items of one warp: 32 / gs proposals.
+#define PROPOSAL_LOOP(np)                                                                                  \
+    const int gs = a.gs, per = 32 / gs;                                                                   \
+    const int lane = threadIdx.x & 31, l = lane & (gs - 1);                                               \
+    const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;                      \
+    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;                                     \
+    for (long long b0 = warp0 * per; b0 < (np); b0 += nwarp * per)
+
+__device__ __forceinline__ long long group_sum64(long long x, int gs)
+{
+    for (int o = gs >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+}
+
+// Singleton guard, and staged deltas of the kept proposals.  Staging never
+// fails: if the table runs short of slots the sweep is abandoned
+// (st->overflow) before anything is committed, and the sweep end schedules a
+// larger table and a retry.
 __global__ void k_stage(SweepArgs a)
 {
     extern __shared__ long long dyn_jobs[];
@@ -546,22 +583,24 @@ __global__ void k_stage(SweepArgs a)
     JobAcc acc(job_smem_init(a.jobs, dyn_jobs), reinterpret_cast<long long*>(&a.js[0].np1), kJobStride);
     const unsigned long long mask = st->mask;
     const long long np = (long long)st->nprop;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
-        const long long p = base + threadIdx.x;
+    PROPOSAL_LOOP(np)
+    {
+        const long long p = b0 + lane / gs;
         int job = -1, ins_count = 0;
         if (p < np) {
             const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
             const bool keep = !(a.size[ca] == 1 && a.size[cb] == 1) || cb < ca;
-            a.pflag[p] = keep ? 1 : 0;
+            if (l == 0) a.pflag[p] = keep ? 1 : 0;
             if (keep) {
                 const int j = a.jid[v];
-                job = j;
                 const JobInfo& J = a.job[j];
-                atomicAdd(&a.dsize[ca], -1);
-                atomicAdd(&a.dsize[cb], 1);
+                if (l == 0) {
+                    job = j;
+                    atomicAdd(&a.dsize[ca], -1);
+                    atomicAdd(&a.dsize[cb], 1);
+                }
                 const int* gv = a.G + row_of(J, v);
-                for (int i = 0; i < J.k; ++i) {
+                for (int i = l; i < J.k; i += gs) {
                     const int g = gv[i];
                     bool ins = false;
                     const long long sa = table_find(a.table, mask, ckey(ca, g));
@@ -595,27 +634,35 @@ __global__ void k_eval(SweepArgs a)
     JobAcc acc(job_smem_init(a.jobs, dyn_jobs), &a.js[0].dF, kJobStride);
     const unsigned long long mask = st->mask;
     const long long np = (long long)st->nprop;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
-        if (!a.pflag[p]) continue;
-        const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
-        const int job = a.jid[v];
-        const JobInfo& J = a.job[job];
-        const int* gv = a.G + row_of(J, v);
-        long long keys = 0;
-        for (int i = 0; i < J.k; ++i) {
-            const int g = gv[i];
-            const long long sa = table_find(a.table, mask, ckey(ca, g));
-            const long long sb = table_find(a.table, mask, ckey(cb, g));
-            if (sa < 0 || sb < 0) {
-                set_err(st, CC_ERR_INVALID);  // staged keys must exist
-                continue;
+    PROPOSAL_LOOP(np)
+    {
+        const long long p = b0 + lane / gs;
+        long long keys = 0, sizes = 0;
+        int job = -1;
+        if (p < np && a.pflag[p]) {
+            const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
+            const int j = a.jid[v];
+            const JobInfo& J = a.job[j];
+            const int* gv = a.G + row_of(J, v);
+            for (int i = l; i < J.k; i += gs) {
+                const int g = gv[i];
+                const long long sa = table_find(a.table, mask, ckey(ca, g));
+                const long long sb = table_find(a.table, mask, ckey(cb, g));
+                if (sa < 0 || sb < 0) {
+                    set_err(st, CC_ERR_INVALID);  // staged keys must exist
+                    continue;
+                }
+                const Slot* A = a.table + sa;
+                const Slot* B = a.table + sb;
+                keys += -(2LL * A->cnt + A->dlt) + (2LL * B->cnt + B->dlt);
             }
-            const Slot* A = a.table + sa;
-            const Slot* B = a.table + sb;
-            keys += -(2LL * A->cnt + A->dlt) + (2LL * B->cnt + B->dlt);
+            if (l == 0) {
+                job = j;
+                sizes = (long long)J.k * (-(2LL * a.size[ca] + a.dsize[ca]) + (2LL * a.size[cb] + a.dsize[cb]));
+            }
         }
-        acc.add(job, -2 * keys + (long long)J.k * (-(2LL * a.size[ca] + a.dsize[ca]) + (2LL * a.size[cb] + a.dsize[cb])));
+        keys = group_sum64(keys, gs);
+        if (job >= 0) acc.add(job, -2 * keys + sizes);
     }
     job_acc_finish(acc, a.jobs);
 }
@@ -647,8 +694,8 @@ __global__ void k_decide(SweepArgs a)
     }
 }
 
-// Thread per proposal of a job that falls back to the matching (mode 2):
-// undo its staged deltas (light sweeps) and bid its (dD, v) at both clusters.
+// Proposals of a job that falls back to the matching (mode 2): undo their
+// staged deltas (light sweeps) and bid (dD, v) at both clusters.
 __global__ void k_bid(SweepArgs a)
 {
     DevState* st = a.st;
@@ -656,27 +703,33 @@ __global__ void k_bid(SweepArgs a)
     const bool staged = !st->heavy;
     const unsigned long long mask = st->mask;
     const long long np = (long long)st->nprop;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+    PROPOSAL_LOOP(np)
+    {
+        const long long p = b0 + lane / gs;
+        if (p >= np) continue;
         const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
         const int j = a.jid[v];
         if (a.js[j].mode != 2) continue;
         if (staged && a.pflag[p]) {
             const JobInfo& J = a.job[j];
             const int* gv = a.G + row_of(J, v);
-            for (int i = 0; i < J.k; ++i) {
+            for (int i = l; i < J.k; i += gs) {
                 const int g = gv[i];
                 const long long sa = table_find(a.table, mask, ckey(ca, g));
                 const long long sb = table_find(a.table, mask, ckey(cb, g));
                 if (sa >= 0) a.table[sa].dlt = 0;
                 if (sb >= 0) a.table[sb].dlt = 0;
             }
-            a.dsize[ca] = 0;
-            a.dsize[cb] = 0;
+            if (l == 0) {
+                a.dsize[ca] = 0;
+                a.dsize[cb] = 0;
+            }
         }
-        const unsigned long long key = pack_key(a.pg[p], v);
-        atomicMin(&a.best[ca], key);
-        atomicMin(&a.best[cb], key);
+        if (l == 0) {
+            const unsigned long long key = pack_key(a.pg[p], v);
+            atomicMin(&a.best[ca], key);
+            atomicMin(&a.best[cb], key);
+        }
     }
 }
 
@@ -691,19 +744,19 @@ __global__ void k_match_keys(SweepArgs a)
     if (st->skip || st->err) return;
     const unsigned long long mask = st->mask;
     const long long np = (long long)st->nprop;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
-        const long long p = base + threadIdx.x;
+    PROPOSAL_LOOP(np)
+    {
+        const long long p = b0 + lane / gs;
         int ins_count = 0;
         if (p < np) {
             const int v = a.pv[p], ca = a.pa[p], cb = a.pb[p];
             const int j = a.jid[v];
             const unsigned long long key = pack_key(a.pg[p], v);
             if (a.js[j].mode == 2 && a.best[ca] == key && a.best[cb] == key) {
-                a.pflag[p] = 2;
+                if (l == 0) a.pflag[p] = 2;
                 const JobInfo& J = a.job[j];
                 const int* gv = a.G + row_of(J, v);
-                for (int i = 0; i < J.k; ++i) {
+                for (int i = l; i < J.k; i += gs) {
                     bool ins = false;
                     if (table_find_or_insert(a.table, mask, ckey(cb, gv[i]), &ins) < 0) st->overflow = 1;
                     ins_count += ins;
@@ -714,9 +767,9 @@ __global__ void k_match_keys(SweepArgs a)
     }
 }
 
-// Thread per proposal: the light commit of P1 (mode 1: C, the staged size
-// and count deltas folded in) or the move of a matching winner (mode 2).
-// Skipped entirely after an overflow.
+// The light commit of P1 (mode 1: C, the staged size and count deltas folded
+// in) or the move of a matching winner (mode 2).  Skipped entirely after an
+// overflow.
 __global__ void k_commit(SweepArgs a)
 {
     extern __shared__ long long dyn_jobs[];
@@ -731,9 +784,9 @@ __global__ void k_commit(SweepArgs a)
     JobAcc df(sh ? sh + a.jobs : nullptr, &a.js[0].dF, kJobStride);
     const unsigned long long mask = st->mask;
     const long long np = (long long)st->nprop;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < np; base += stride) {
-        const long long p = base + threadIdx.x;
+    PROPOSAL_LOOP(np)
+    {
+        const long long p = b0 + lane / gs;
         long long live = 0, dF = 0, moved = 0;
         int job = -1;
         if (p < np) {
@@ -743,12 +796,14 @@ __global__ void k_commit(SweepArgs a)
             const JobInfo& J = a.job[j];
             const int* gv = a.G + row_of(J, v);
             if (mode == 1 && a.pflag[p]) {
-                a.C[v] = cb;
-                int d = atomicExch(&a.dsize[ca], 0);
-                if (d) atomicAdd(&a.size[ca], d);
-                d = atomicExch(&a.dsize[cb], 0);
-                if (d) atomicAdd(&a.size[cb], d);
-                for (int i = 0; i < J.k; ++i) {
+                if (l == 0) {
+                    a.C[v] = cb;
+                    int d = atomicExch(&a.dsize[ca], 0);
+                    if (d) atomicAdd(&a.size[ca], d);
+                    d = atomicExch(&a.dsize[cb], 0);
+                    if (d) atomicAdd(&a.size[cb], d);
+                }
+                for (int i = l; i < J.k; i += gs) {
                     const int g = gv[i];
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
@@ -762,18 +817,20 @@ __global__ void k_commit(SweepArgs a)
                         if (dd) {
                             const int old = atomicAdd(&s->cnt, dd);
                             live += (old == 0) - (old + dd == 0);
-                            summ_update(a, s->key, dd, old + dd);
+                            summ_update(a, s->key, dd);
                         }
                     }
                 }
             } else if (mode == 2 && a.pflag[p] == 2) {
-                job = j;
-                a.C[v] = cb;
-                atomicAdd(&a.size[ca], -1);
-                atomicAdd(&a.size[cb], 1);
-                moved = 1;
-                dF = 2LL * a.pg[p];
-                for (int i = 0; i < J.k; ++i) {
+                if (l == 0) {
+                    job = j;
+                    a.C[v] = cb;
+                    atomicAdd(&a.size[ca], -1);
+                    atomicAdd(&a.size[cb], 1);
+                    moved = 1;
+                    dF = 2LL * a.pg[p];
+                }
+                for (int i = l; i < J.k; i += gs) {
                     const int g = gv[i];
                     const long long sa = table_find(a.table, mask, ckey(ca, g));
                     const long long sb = table_find(a.table, mask, ckey(cb, g));
@@ -784,8 +841,8 @@ __global__ void k_commit(SweepArgs a)
                     const int oa = atomicAdd(&a.table[sa].cnt, -1);
                     const int ob = atomicAdd(&a.table[sb].cnt, 1);
                     live += (ob == 0) - (oa == 1);
-                    summ_update(a, ckey(ca, g), -1, oa - 1);
-                    summ_update(a, ckey(cb, g), 1, ob + 1);
+                    summ_update(a, ckey(ca, g), -1);
+                    summ_update(a, ckey(cb, g), 1);
                 }
             }
         }

@@ -43,7 +43,7 @@ def test_exports_every_declared_symbol(native):
 def test_default_options(native):
     o = native.cc_default_options()
     assert o.max_sweeps == 20 and o.debug_checks == 0 and o.table_log2 == 0 and o.table_start_log2 == 0
-    assert o.sweep_mode == 0 and list(o.reserved) == [0] * 3
+    assert o.sweep_mode == 0 and o.lanes == 0 and list(o.reserved) == [0] * 2
 
 
 def _create_status(native, n, nnz, row_off, col, k, labels, opt=None):
@@ -66,10 +66,15 @@ def test_host_validation(native):
     st, msg = _create_status(native, 300_000_000, 0, ok, None, 3, ok)  # 3 k n + k >= 2^31
     assert st == 4 and "2^31" in msg
     opt = native.cc_default_options()
-    opt.reserved[2] = 7
+    opt.reserved[1] = 7
     assert _create_status(native, 5, 0, ok, None, 1, ok, ctypes.byref(opt))[0] == 1
     opt = native.cc_default_options()
     opt.sweep_mode = 3
+    assert _create_status(native, 5, 0, ok, None, 1, ok, ctypes.byref(opt))[0] == 1
+    opt = native.cc_default_options()
+    opt.lanes = 3
+    assert _create_status(native, 5, 0, ok, None, 1, ok, ctypes.byref(opt))[0] == 1
+    opt.lanes = 64
     assert _create_status(native, 5, 0, ok, None, 1, ok, ctypes.byref(opt))[0] == 1
     opt = native.cc_default_options()
     opt.table_log2 = 99
@@ -163,7 +168,7 @@ def test_server_host_validation(native):
     lib = native.lib
     srv = ctypes.c_void_p(7)
     so = native.cc_server_default_options()
-    assert so.max_active == 4 and so.max_batch_jobs == 256 and so.budget_bytes == 0
+    assert so.max_active == 8 and so.max_batch_jobs == 256 and so.budget_bytes == 0
     so.reserved[1] = 3
     assert lib.cc_server_create(ctypes.byref(so), None, ctypes.byref(srv)) == 1
     assert srv.value is None
@@ -179,3 +184,30 @@ def test_server_host_validation(native):
     assert lib.cc_server_submit(None, None, None, None) == 1
     assert lib.cc_server_progress(None, 0, None, 0, None, None) == 1
     lib.cc_server_destroy(None)
+
+
+def test_plan_batches_host(native):
+    """Batches hold one lane bin each, keep job order within a bin, fit the
+    budget, respect the job cap, and mark jobs over the budget with -1."""
+    sizes = [(1000, 20000, 10), (500, 8000, 3), (2000, 40000, 9), (800, 9000, 60), (700, 7000, 4),
+             (3000, 60000, 8), (900, 9000, 50), (100000, 2000000, 30)]
+    one = [native.cc_estimate_bytes([s])[1] for s in sizes]
+    budget = 3 * max(one[:7])
+    batch, nb = native.cc_plan_batches(sizes, budget)
+    assert batch[7] == -1  # the big job alone exceeds the budget
+    bins = {}
+    for j, b in enumerate(batch[:7]):
+        bins.setdefault(int(b), []).append(j)
+    assert len(bins) == nb
+    lanes = lambda k: next(g for g in (1, 2, 4, 8, 16, 32) if g * 10 >= k or g == 32)  # noqa: E731
+    for b, members in bins.items():
+        assert len({lanes(sizes[j][2]) for j in members}) == 1
+        assert native.cc_estimate_bytes([sizes[j] for j in members])[1] <= budget
+    # bins in increasing order of lanes: k <= 10 first
+    assert batch[1] == batch[4] == 0
+    capped, nb2 = native.cc_plan_batches(sizes[:7], 1 << 40, max_jobs=1)
+    assert nb2 == 7 and sorted(capped.tolist()) == list(range(7))
+    whole, nb3 = native.cc_plan_batches(sizes[:7], 1 << 40)
+    assert nb3 == 2  # bins of k: {10, 3, 9, 4, 8}, {60, 50}
+    with pytest.raises(native.CCError):
+        native.cc_plan_batches([(0, 0, 1)], 1 << 30)

@@ -297,7 +297,7 @@ def test_run_timing_and_launch_count(cc):
         sweep_ms, prop_ms = job.last_run_timing()
         assert len(sweep_ms) == len(prop_ms) == done
         assert np.all(sweep_ms > 0) and np.all(prop_ms > 0) and np.all(prop_ms <= sweep_ms)
-        per_sweep = 19 + 3 * 11  # kernels of one unrolled sweep body
+        per_sweep = 19 + 3 * 8  # kernels of one unrolled sweep body
         assert job.launch_count() - base == 1 + ((done + 3) // 4) * 4 * per_sweep
         job.sweep()
         assert len(job.last_run_timing()[0]) == 1
@@ -370,3 +370,25 @@ def test_table_retry_path(cc):
         assert ts["retries"] >= 1 and ts["rebuilds"] >= 2
         assert ts["live_keys"] <= ts["used_slots"] <= ts["capacity"] <= ts["max_capacity"]
         assert job.objective_recompute() == ref.F
+
+
+def test_full_size_lfr_as_benchmarked(cc):
+    """The benchmark workload at full size (LFR-style n = 1,000,000, k = 20),
+    launched as bench.py launches it (a caller stream, graphs of up to 4
+    sweeps, reset then run to convergence, twice): every sweep record, the
+    raw ids, the labels and F equal the oracle's."""
+    import torch
+
+    c = make_config("lfr")
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    ref = oracle.sync_run(ro, col, lab, 20)
+    stream = torch.cuda.Stream()
+    with cc.Consensus(ro, col, lab) as job:
+        job.set_stream(stream.cuda_stream)
+        for _ in range(2):
+            job.reset()
+            assert job.run_until_converged(20) == ref.sweeps
+            assert job.history() == ref.stats
+            np.testing.assert_array_equal(job.cluster_ids(), ref.C)
+        assert job.objective() == ref.F == job.objective_recompute()
+        np.testing.assert_array_equal(job.consensus_labels(), oracle.renumber(ref.C))

@@ -129,10 +129,25 @@ def test_serve_oversize_job_fails_alone(cc):
 
 
 def test_serve_bins_by_k(cc):
-    """Jobs of very different k go to different contexts (lane bins)."""
-    lo = _jobs(6, 7, kmin=2, kmax=5)
-    hi = _jobs(6, 8, kmin=50, kmax=64)
+    """Jobs of very different k go to different contexts (lane bins); with
+    sizes alike, each bin is one context."""
+    lo = _jobs(6, 7, nmin=1000, nmax=1100, kmin=2, kmax=5)
+    hi = _jobs(6, 8, nmin=1000, nmax=1100, kmin=50, kmax=64)
     jobs = [j for pair in zip(lo, hi) for j in pair]
+    refs = _refs(jobs)
+    with cc.Server(max_active=2, max_batch_jobs=64) as srv:
+        tickets = [srv.submit(*j) for j in jobs]
+        srv.drain()
+        _check(srv, tickets, jobs, refs)
+        assert srv.stats()["batches"] == 2
+
+
+def test_serve_size_classes(cc):
+    """A job joins a context only if its n is within a factor 4 of the first
+    job's, so a small job never waits for a large one."""
+    small = _jobs(4, 10, nmin=200, nmax=220, kmin=10, kmax=10)
+    large = _jobs(4, 11, nmin=5000, nmax=5200, kmin=10, kmax=10)
+    jobs = [j for pair in zip(small, large) for j in pair]
     refs = _refs(jobs)
     with cc.Server(max_active=2, max_batch_jobs=64) as srv:
         tickets = [srv.submit(*j) for j in jobs]
