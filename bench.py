@@ -222,6 +222,19 @@ def cpu_baseline(c):
             "sample": f"whole job: {r.sweeps} synchronous sweeps from the singleton start ({dt:.1f} s)"}, r
 
 
+def over_ranks(dist, seconds, units, device):
+    """Whole-job figures of N replicas: the slowest rank's time and the units
+    of all ranks (each rank runs its own copy of the job; nothing else is
+    exchanged)."""
+    import torch
+
+    t = torch.tensor([seconds, units], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(t[1])
+
+
 def mix_pool(args):
     """Specs of the batched / served mix, the pool job each spec draws, and the pool."""
     from workloads.configs import batch_job_specs, serve_job_specs
@@ -538,11 +551,7 @@ def main():
     launches = job.launch_count() - launches0
     units = float(nnz) * k * sweeps_total
     if dist:
-        t = torch.tensor([ms, units], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms, units = float(mx[0]), float(t[1])
+        ms, units = over_ranks(dist, ms, units, "cuda")
     value = units / (ms / 1e3)
 
     # untimed instrumentation: the start state of every sweep, for the
@@ -587,11 +596,7 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_units = float(nnz) * k * e2e_sweeps
     if dist:
-        t = torch.tensor([e2e_s, e2e_units], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        e2e_s, e2e_units = float(mx[0]), float(t[1])
+        e2e_s, e2e_units = over_ranks(dist, e2e_s, e2e_units, "cuda")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

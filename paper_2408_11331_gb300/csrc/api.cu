@@ -82,6 +82,8 @@ void free_all(cc_ctx* c)
     c->chunk_done = nullptr;
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     c->own_stream = nullptr;
+    if (c->body_stream) cudaStreamDestroy(c->body_stream);
+    c->body_stream = nullptr;
 }
 
 unsigned long long next_pow2(unsigned long long x)
@@ -157,6 +159,7 @@ cc_status start_state(cc_ctx* c)
         if (rp != CC_OK) return rp;
         s.rebuilds = prev.rebuilds;
         s.retries = prev.retries;
+        s.region_launches = prev.region_launches;
     }
     c->started = true;
     s.stop = 1;
@@ -206,9 +209,15 @@ cc_status ensure_graph(cc_ctx* c, int limit, RunGraph** out)
     for (int s = 0; s < limit && e == cudaSuccess; ++s) {
         e = cudaEventRecordWithFlags(g.bound[s], c->own_stream, cudaEventRecordExternal);
         if (e == cudaSuccess)
-            e = launch_sweep(c->args, c->rows, c->grid, c->own_stream, g.prop[2 * s], g.prop[2 * s + 1]);
+            e = launch_sweep(c->args, c->rows, c->grid, c->own_stream, g.prop[2 * s], g.prop[2 * s + 1],
+                             c->body_stream);
     }
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(g.bound[limit], c->own_stream, cudaEventRecordExternal);
+    cudaStreamCaptureStatus bs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->body_stream, &bs) == cudaSuccess && bs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t body = nullptr;
+        cudaStreamEndCapture(c->body_stream, &body);  // a region left open by a failed capture
+    }
     cudaError_t e2 = cudaStreamEndCapture(c->own_stream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -249,7 +258,7 @@ cc_status run(cc_ctx* c, int limit, int* done)
     // so the number of launches is bounded by the limit plus the retries
     for (int launch = 0; launch < limit + 64; ++launch) {
         CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
-        c->launches += (long long)chunk * kKernelsPerSweep;
+        c->launches += (long long)chunk * kKernelsOutsideRegions;
         r = read_state(c, &st);
         if (r != CC_OK) return r;
         const int ran = st.run_bodies - before;
@@ -426,6 +435,7 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     CC_TRY(cudaGetDevice(&c->device));
     CC_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     CC_TRY(cudaStreamCreateWithPriority(&c->own_stream, cudaStreamNonBlocking, priority));
+    CC_TRY(cudaStreamCreateWithPriority(&c->body_stream, cudaStreamNonBlocking, priority));
     // pooled memory is allocated in the order of the context's own stream, so
     // such a context runs on that stream
     c->stream = (stream && !pool) ? static_cast<cudaStream_t>(stream) : c->own_stream;
@@ -766,7 +776,7 @@ cc_status launch_chunk(cc_ctx* c)
     cc_status r = ensure_graph(c, chunk, &g);
     if (r != CC_OK) return r;
     CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
-    c->launches += (long long)chunk * kKernelsPerSweep;
+    c->launches += (long long)chunk * kKernelsOutsideRegions;
     CC_CUDA(c, cudaMemcpyAsync(c->hstate, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
     CC_CUDA(c, cudaEventRecord(c->chunk_done, c->stream));
     c->async_launches += 1;
@@ -1052,7 +1062,13 @@ cc_status cc_table_stats(cc_ctx* c, cc_table_info* out)
 cc_status cc_launch_count(const cc_ctx* c, int64_t* out)
 {
     if (!c || !out) return fail(nullptr, CC_ERR_INVALID, "null argument");
-    *out = c->launches;
+    // kernels outside the sweep graphs' regions are counted here, those of
+    // the regions that ran by their gates on the device
+    cc_ctx* m = const_cast<cc_ctx*>(c);
+    DevState s;
+    cc_status r = read_state(m, &s);
+    if (r != CC_OK) return r;
+    *out = c->launches + (int64_t)s.region_launches;
     return CC_OK;
 }
 

@@ -101,6 +101,7 @@ struct DevState {
     int tvalid;                  // 1: the table holds the counts of the current C
     int run_limit;               // sweep limit of the current run
     int run_bodies;              // sweeps of the current run that did work (retried ones included)
+    unsigned long long region_launches;  // kernels run inside the gated regions of sweep graphs
 };
 
 // Arguments of the kernels (passed by value).
@@ -393,11 +394,18 @@ void set_thread_error(const std::string& msg);
 // ---- sweep.cu ----
 cudaError_t launch_run_begin(const SweepArgs& a, int limit, cudaStream_t s);
 // One sweep of every job; prop0/prop1 (may be null) are recorded around the
-// proposal kernels.
+// proposal kernels.  With a body stream (while s is being captured into a
+// graph), the heavy path, its rollback, the light path and the end-of-sweep
+// rebuild become IF regions of the graph, each behind a one-thread gate
+// kernel, so a sweep launches only the regions it needs.
 constexpr int kKernelsPerRebuild = 8;
-constexpr int kKernelsPerSweep = 19 + 3 * kKernelsPerRebuild;
+constexpr int kKernelsPerSweep = 19 + 3 * kKernelsPerRebuild;  // kernels of a sweep without regions
+constexpr int kGatesPerSweep = 4;
+// kernels of a sweep graph outside its regions (gates included); the kernels
+// of the regions that run are counted on the device (DevState.region_launches)
+constexpr int kKernelsOutsideRegions = kKernelsPerSweep + kGatesPerSweep - (12 + 9 + 3 + kKernelsPerRebuild);
 cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaEvent_t prop0,
-                         cudaEvent_t prop1);
+                         cudaEvent_t prop1, cudaStream_t body = nullptr);
 cudaError_t prepare_propose(int* blocks_per_sm);
 
 }  // namespace ccg

@@ -23,6 +23,7 @@ struct cc_ctx {
     int device = 0, sms = 0;
     cudaStream_t stream = nullptr;      // stream used by calls
     cudaStream_t own_stream = nullptr;  // stream created by the context (also used for capture)
+    cudaStream_t body_stream = nullptr; // captures the bodies of a sweep graph's conditional regions
     cudaMemPool_t pool = nullptr;       // device memory comes from this pool (stream-ordered) if set
     std::vector<ccg::JobInfo> job;      // host copy of the job table
     std::vector<long long> F0;          // objective of each job at the singleton start

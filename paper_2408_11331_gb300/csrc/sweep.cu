@@ -117,74 +117,97 @@ __device__ __forceinline__ int group_sum(int x, int gs)
     return x;
 }
 
-// Summary part of A_x(v) for a non-singleton cluster x (size sx) of job J,
-// lanes of a group over the partitions i = l, l + gs, ...: ex = sum of m where
-// v carries the row's label d (exact there), ub = ex + sum of (sx - m)
-// elsewhere: the members not carrying d bound the count of any other label,
-// so ub is an upper bound on A_x.
+// The partitions of a job are scored four at a time ("quads"): partition
+// 4q + t is component t of quad q of v's label row (one int4 load) and entry
+// 4q + t of x's summary row (two int4 loads of {d, m} pairs).  Rows are kp =
+// k rounded up to 4 entries, so only the last quad can hold padding, which
+// is masked out (4q + t >= k).  Lane l of a group takes quads l, l + gs, ...
+
+// Adds partition t of a quad to the summary sums.
+__device__ __forceinline__ void summary_one(int g, int d, int m, bool on, int sx, int& ex, int& ub)
+{
+    if (!on) return;
+    const bool eq = g == d;
+    ex += eq ? m : 0;
+    ub += eq ? m : sx - m;
+}
+
+// Summary part of A_x(v) for a non-singleton cluster x (size sx) of job J:
+// ex = sum of m where v carries the row's label d (exact there), ub = ex +
+// sum of (sx - m) elsewhere: the members not carrying d bound the count of
+// any other label, so ub is an upper bound on A_x.
 __device__ __forceinline__ void summary_part(const SweepArgs& a, const JobInfo& J, const int* __restrict__ gv, int x,
                                              int sx, int l, int gs, int& ex, int& ub)
 {
     ex = 0;
     ub = 0;
-    const int2* S = a.summ + row_of(J, x);
-    for (int i0 = l; i0 < J.k; i0 += gs * kInflight) {
-        int2 r[kInflight];
-        int g[kInflight];
+    const int4* G4 = reinterpret_cast<const int4*>(gv);
+    const int4* S4 = reinterpret_cast<const int4*>(a.summ + row_of(J, x));
+    const int kq = J.kp >> 2, k = J.k;
+    constexpr int kQuads = 2;  // quads per lane in flight
+    for (int q0 = l; q0 < kq; q0 += gs * kQuads) {
+        int4 g[kQuads], s0[kQuads], s1[kQuads];
 #pragma unroll
-        for (int b = 0; b < kInflight; ++b) {
-            const int i = i0 + b * gs;
-            r[b] = make_int2(-1, 0);
-            g[b] = -2;
-            if (i < J.k) {
-                r[b] = __ldg(S + i);
-                g[b] = __ldg(gv + i);
+        for (int b = 0; b < kQuads; ++b) {
+            const int q = q0 + b * gs;
+            g[b] = make_int4(-1, -1, -1, -1);
+            s0[b] = make_int4(-2, 0, -2, 0);
+            s1[b] = s0[b];
+            if (q < kq) {
+                g[b] = __ldg(G4 + q);
+                s0[b] = __ldg(S4 + 2 * q);
+                s1[b] = __ldg(S4 + 2 * q + 1);
             }
         }
 #pragma unroll
-        for (int b = 0; b < kInflight; ++b) {
-            if (i0 + b * gs < J.k) {
-                const bool eq = g[b] == r[b].x;
-                ex += eq ? r[b].y : 0;
-                ub += eq ? r[b].y : sx - r[b].y;
-            }
+        for (int b = 0; b < kQuads; ++b) {
+            const int i = 4 * (q0 + b * gs);
+            summary_one(g[b].x, s0[b].x, s0[b].y, i < k, sx, ex, ub);
+            summary_one(g[b].y, s0[b].z, s0[b].w, i + 1 < k, sx, ex, ub);
+            summary_one(g[b].z, s1[b].x, s1[b].y, i + 2 < k, sx, ex, ub);
+            summary_one(g[b].w, s1[b].z, s1[b].w, i + 3 < k, sx, ex, ub);
         }
     }
 }
 
-// Exact counts of the partitions the summary leaves open (v does not carry
-// the row's label and some member of x does not carry it either), by hash
-// probes.
+// Starts the probe of partition t of a quad if the summary leaves it open (v
+// does not carry the row's label and some member of x does not carry it
+// either): the key, its first slot and that slot's contents.
+__device__ __forceinline__ bool probe_start(const Slot* __restrict__ table, unsigned long long mask, int x, int g,
+                                            int d, int m, bool on, int sx, unsigned long long& key,
+                                            unsigned long long& h, ulonglong2& ev)
+{
+    if (!on || g == d || sx <= m) return false;
+    key = ckey(x, g);
+    h = hash_key(key) & mask;
+    ev = __ldg(reinterpret_cast<const ulonglong2*>(table + h));
+    return true;
+}
+
+// Exact counts of the partitions the summary leaves open, by hash probes
+// (four in flight per lane).
 __device__ __forceinline__ int probe_part(const SweepArgs& a, const JobInfo& J, const Slot* __restrict__ table,
                                           unsigned long long mask, const int* __restrict__ gv, int x, int sx, int l,
                                           int gs)
 {
-    const int2* S = a.summ + row_of(J, x);
+    const int4* G4 = reinterpret_cast<const int4*>(gv);
+    const int4* S4 = reinterpret_cast<const int4*>(a.summ + row_of(J, x));
+    const int kq = J.kp >> 2, k = J.k;
     int acc = 0;
-    for (int i0 = l; i0 < J.k; i0 += gs * kInflight) {
-        unsigned long long key[kInflight], h[kInflight];
-        ulonglong2 ev[kInflight];
-        bool on[kInflight];
+    for (int q = l; q < kq; q += gs) {
+        const int4 g = __ldg(G4 + q);
+        const int4 s0 = __ldg(S4 + 2 * q);
+        const int4 s1 = __ldg(S4 + 2 * q + 1);
+        const int i = 4 * q;
+        unsigned long long key[4] = {0, 0, 0, 0}, h[4] = {0, 0, 0, 0};
+        ulonglong2 ev[4];
+        bool on[4];
+        on[0] = probe_start(table, mask, x, g.x, s0.x, s0.y, i < k, sx, key[0], h[0], ev[0]);
+        on[1] = probe_start(table, mask, x, g.y, s0.z, s0.w, i + 1 < k, sx, key[1], h[1], ev[1]);
+        on[2] = probe_start(table, mask, x, g.z, s1.x, s1.y, i + 2 < k, sx, key[2], h[2], ev[2]);
+        on[3] = probe_start(table, mask, x, g.w, s1.z, s1.w, i + 3 < k, sx, key[3], h[3], ev[3]);
 #pragma unroll
-        for (int b = 0; b < kInflight; ++b) {
-            const int i = i0 + b * gs;
-            on[b] = false;
-            key[b] = 0;
-            h[b] = 0;
-            ev[b] = make_ulonglong2(kEmpty, 0ull);
-            if (i < J.k) {
-                const int2 r = __ldg(S + i);
-                const int g = __ldg(gv + i);
-                on[b] = g != r.x && sx > r.y;
-                if (on[b]) {
-                    key[b] = ckey(x, g);
-                    h[b] = hash_key(key[b]) & mask;
-                    ev[b] = __ldg(reinterpret_cast<const ulonglong2*>(table + h[b]));
-                }
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < kInflight; ++b)
+        for (int b = 0; b < 4; ++b)
             if (on[b]) acc += resolve(table, mask, key[b], h[b], ev[b]);
     }
     return acc;
@@ -280,7 +303,7 @@ struct EdgeScratch {
 // group reductions are outside the branches, so every lane of the warp takes
 // part in every shuffle.
 template <bool kSingle>
-__global__ void __launch_bounds__(kBlock) k_edges(SweepArgs a)
+__global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
 {
     DevState* st = a.st;
     if (st->skip) return;
@@ -940,6 +963,64 @@ __global__ void k_end(SweepArgs a)
     }
 }
 
+// Regions of a sweep that run only when needed.  In a captured graph each is
+// an IF node whose condition a one-thread gate kernel sets from the control
+// block, so a sweep that does not need a region skips its launches instead of
+// running kernels that return at once.
+enum Gate { kGateHeavy = 0, kGateRollback = 1, kGateLight = 2, kGateRebuild = 3 };
+
+__global__ void k_gate(cudaGraphConditionalHandle h, DevState* st, int which, int kernels)
+{
+    const bool run = !st->skip && !st->err;
+    bool on = false;
+    if (which == kGateHeavy) on = run && st->heavy;
+    else if (which == kGateRollback) on = run && st->heavy && st->rollback;
+    else if (which == kGateLight) on = run && !st->heavy && st->nprop > 0;
+    else on = st->rebuild && !st->err;
+    if (on) st->region_launches += (unsigned long long)kernels;
+    cudaGraphSetConditional(h, on ? 1u : 0u);
+}
+
+// Opens an IF region in the graph being captured on s: the gate kernel, then
+// the conditional node, whose body is captured on b until close_region.
+cudaError_t open_region(cudaStream_t s, cudaStream_t b, DevState* st, Gate which, int kernels)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureUnsupported;
+    cudaGraphConditionalHandle h = 0;
+    e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+    if (e != cudaSuccess) return e;
+    k_gate<<<1, 1, 0, s>>>(h, st, (int)which, kernels);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, deps, edges, nd, &p);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    return cudaStreamBeginCaptureToGraph(b, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal);
+}
+
+cudaError_t close_region(cudaStream_t b)
+{
+    cudaGraph_t g = nullptr;
+    return cudaStreamEndCapture(b, &g);
+}
+
 inline int jobs_grid(int jobs)
 {
     int g = (jobs + 255) / 256;
@@ -969,14 +1050,25 @@ cudaError_t launch_run_begin(const SweepArgs& a, int limit, cudaStream_t s)
 }
 
 cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaEvent_t prop0,
-                         cudaEvent_t prop1)
+                         cudaEvent_t prop1, cudaStream_t body)
 {
     const int g2 = grid;
     const int jg = jobs_grid(a.jobs);
     const size_t js1 = smem_jobs_bytes(a.jobs);
+    cudaError_t e = cudaSuccess;
+    // with a body stream, the optional regions are IF nodes of the captured
+    // graph (their kernels also check the control block themselves)
+    auto open = [&](Gate which, int kernels) -> cudaStream_t {
+        if (!body || e != cudaSuccess) return s;
+        e = open_region(s, body, a.st, which, kernels);
+        return body;
+    };
+    auto close = [&]() {
+        if (body && e == cudaSuccess) e = close_region(body);
+    };
     k_begin<<<jg, 256, 0, s>>>(a);
     if (prop0) {
-        cudaError_t e = cudaEventRecordWithFlags(prop0, s, cudaEventRecordExternal);
+        e = cudaEventRecordWithFlags(prop0, s, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
     if (a.jobs == 1) {
@@ -988,22 +1080,41 @@ cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStrea
     }
     k_collect<<<grid, kBlock, js1, s>>>(a);
     if (prop1) {
-        cudaError_t e = cudaEventRecordWithFlags(prop1, s, cudaEventRecordExternal);
+        e = cudaEventRecordWithFlags(prop1, s, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
     k_route<<<1, 1, 0, s>>>(a);
-    k_h_mark<<<g2, kBlock, js1, s>>>(a);
-    k_h_apply<<<g2, kBlock, 0, s>>>(a, 0);
-    cudaError_t e = launch_table_rebuild(a, rows, true, s, true);
-    if (e != cudaSuccess) return e;
-    k_h_eval<<<g2, kBlock, js1, s>>>(a);
-    k_h_decide<<<jg, 256, 0, s>>>(a);
-    k_h_apply<<<g2, kBlock, 0, s>>>(a, 1);
-    e = launch_table_rebuild(a, rows, true, s);
-    if (e != cudaSuccess) return e;
-    k_stage<<<g2, kBlock, js1, s>>>(a);
-    k_eval<<<g2, kBlock, js1, s>>>(a);
-    k_decide<<<jg, 256, 0, s>>>(a);
+    {
+        cudaStream_t r = open(kGateHeavy, 4 + kKernelsPerRebuild);
+        if (e != cudaSuccess) return e;
+        k_h_mark<<<g2, kBlock, js1, r>>>(a);
+        k_h_apply<<<g2, kBlock, 0, r>>>(a, 0);
+        e = launch_table_rebuild(a, rows, true, r, true);
+        if (e != cudaSuccess) return e;
+        k_h_eval<<<g2, kBlock, js1, r>>>(a);
+        k_h_decide<<<jg, 256, 0, r>>>(a);
+        close();
+        if (e != cudaSuccess) return e;
+    }
+    {
+        cudaStream_t r = open(kGateRollback, 1 + kKernelsPerRebuild);
+        if (e != cudaSuccess) return e;
+        k_h_apply<<<g2, kBlock, 0, r>>>(a, 1);
+        e = launch_table_rebuild(a, rows, true, r);
+        if (e != cudaSuccess) return e;
+        close();
+        if (e != cudaSuccess) return e;
+    }
+    {
+        cudaStream_t r = open(kGateLight, 3);
+        if (e != cudaSuccess) return e;
+        k_stage<<<g2, kBlock, js1, r>>>(a);
+        k_eval<<<g2, kBlock, js1, r>>>(a);
+        k_decide<<<jg, 256, 0, r>>>(a);
+        e = cudaGetLastError();
+        close();
+        if (e != cudaSuccess) return e;
+    }
     k_bid<<<g2, kBlock, 0, s>>>(a);
     k_match_keys<<<g2, kBlock, 0, s>>>(a);
     k_commit<<<g2, kBlock, 2 * a.jobs <= kSmemJobs ? 2 * smem_jobs_bytes(a.jobs) : 0, s>>>(a);
@@ -1012,7 +1123,14 @@ cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStrea
     k_end<<<1, 1, 0, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_table_rebuild(a, rows, true, s);
+    {
+        cudaStream_t r = open(kGateRebuild, kKernelsPerRebuild);
+        if (e != cudaSuccess) return e;
+        e = launch_table_rebuild(a, rows, true, r);
+        if (e != cudaSuccess) return e;
+        close();
+    }
+    return e;
 }
 
 }  // namespace ccg

@@ -289,7 +289,8 @@ def test_create_from_device_buffers(cc):
 
 def test_run_timing_and_launch_count(cc):
     """Per-sweep device times come from events inside the run's graph; the
-    launch counter counts every kernel node of every run."""
+    launch counter counts the kernels outside the graph's conditional regions
+    on every sweep body and the region kernels that ran."""
     c = make_config("sbm")
     with cc.Consensus(c["row_off"], c["col"], c["labels"]) as job:
         base = job.launch_count()
@@ -297,8 +298,15 @@ def test_run_timing_and_launch_count(cc):
         sweep_ms, prop_ms = job.last_run_timing()
         assert len(sweep_ms) == len(prop_ms) == done
         assert np.all(sweep_ms > 0) and np.all(prop_ms > 0) and np.all(prop_ms <= sweep_ms)
-        per_sweep = 19 + 3 * 8  # kernels of one unrolled sweep body
-        assert job.launch_count() - base == 1 + ((done + 3) // 4) * 4 * per_sweep
+        bodies = ((done + 3) // 4) * 4  # graphs of 4 unrolled sweep bodies
+        outside = 15  # per body: begin, own, edges, collect, route, 4 gates, bid, match keys, commit,
+        #               match reset, end jobs, end
+        regions = 12 + 9 + 3 + 8  # heavy path, rollback, light path, end-of-sweep rebuild
+        delta = job.launch_count() - base
+        assert 1 + bodies * outside < delta < 1 + bodies * (outside + regions)
+        # a sweep runs the heavy or the light path, never both, and the
+        # skipped bodies after the run stopped enter no region
+        assert delta <= 1 + bodies * outside + done * (12 + 9 + 8)
         job.sweep()
         assert len(job.last_run_timing()[0]) == 1
 
