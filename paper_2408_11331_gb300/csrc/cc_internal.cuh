@@ -333,6 +333,53 @@ __device__ __forceinline__ long long table_find_or_insert(Slot* t, unsigned long
     return -1;
 }
 
+// 16-byte compare-and-swap of a whole slot (PTX atom.cas.b128, sm_90 and
+// later): returns the slot's previous contents; the swap happened iff they
+// equal cmp.
+__device__ __forceinline__ ulonglong2 slot_cas(Slot* p, ulonglong2 cmp, ulonglong2 val)
+{
+    ulonglong2 old;
+    asm volatile(
+        "{\n\t"
+        ".reg .b128 c, v, d;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 v, {%4, %5};\n\t"
+        "atom.relaxed.gpu.global.cas.b128 d, [%6], c, v;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t"
+        "}"
+        : "=l"(old.x), "=l"(old.y)
+        : "l"(cmp.x), "l"(cmp.y), "l"(val.x), "l"(val.y), "l"(p)
+        : "memory");
+    return old;
+}
+
+// Adds cnt to key's count in a table being built from a cleared state (every
+// slot either empty with count 0, or holding a key): a new key is written
+// together with its count by one 16-byte CAS; an existing key gets an atomic
+// add.  *inserted is set when this call created the slot.  Returns -1 if the
+// table is full.
+__device__ __forceinline__ long long table_build_add(Slot* t, unsigned long long mask, unsigned long long key, int cnt,
+                                                     bool* inserted)
+{
+    *inserted = false;
+    const ulonglong2 empty = make_ulonglong2(kEmpty, 0ull);
+    const ulonglong2 mine = make_ulonglong2(key, (unsigned long long)(unsigned)cnt);
+    unsigned long long h = hash_key(key) & mask;
+    for (unsigned long long p = 0; p <= mask; ++p) {
+        const ulonglong2 old = slot_cas(t + h, empty, mine);
+        if (old.x == kEmpty && old.y == 0ull) {
+            *inserted = true;
+            return (long long)h;
+        }
+        if (old.x == key) {
+            atomicAdd(&t[h].cnt, cnt);
+            return (long long)h;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
 // ---- setup.cu ----
 // Union assembly: per-job inputs were copied into staging buffers (offsets of
 // job j at offstage[vo_j + j ..], n_j + 1 entries; columns job-local at

@@ -378,9 +378,7 @@ __global__ void k_table_build(SweepArgs a, int conditional)
             const unsigned same = __match_any_sync(0xffffffffu, key);
             bool ins = false;
             if (on && (__ffs(same) - 1) == lane) {
-                const long long s = table_find_or_insert(a.table, mask, key, &ins);
-                if (s < 0) set_err(st, CC_ERR_TABLE_FULL);
-                else atomicAdd(&a.table[s].cnt, __popc(same));
+                if (table_build_add(a.table, mask, key, __popc(same), &ins) < 0) set_err(st, CC_ERR_TABLE_FULL);
             }
             used += __popc(__ballot_sync(0xffffffffu, ins));
         }
