@@ -286,22 +286,27 @@ __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
     }
 }
 
-// Foreign CSR entries of one warp, compacted in shared memory.
+// Kept CSR entries of one warp, compacted in shared memory: up to kChunks
+// chunks of 32 entries are gathered before scoring, so that the scoring
+// rounds (32 / gs candidates each) run nearly full.
+constexpr int kChunks = 4;
 struct EdgeScratch {
-    int v[32], u[32], x[32], sx[32], sa[32], Aa[32], j[32];
+    int v[32 * kChunks], u[32 * kChunks], x[32 * kChunks], sx[32 * kChunks], sa[32 * kChunks], Aa[32 * kChunks],
+        j[32 * kChunks];
 };
 
 // CSR entries 32 at a time per warp: each lane reads one entry (v, u) and
 // keeps it if v's job runs and u lies in another cluster than v (self-loops
-// and repeats of the same (v, C[u]) inside the warp are dropped, and so is a
-// candidate whose gain is >= 0 even with A_x at its bound k |x|); the kept
-// entries are then scored by groups of lanes.  A singleton {u} is scored from
-// the two label rows; another cluster from its summary rows, then (unless the
-// lower bound on dD from the summary is already >= 0, in which case the move
-// can never be proposed) from probes of the open partitions.  A move with
-// dD < 0 bids its packed (dD, C[u]) at best[v] with an atomic minimum.  All
-// group reductions are outside the branches, so every lane of the warp takes
-// part in every shuffle.
+// and repeats of the same (v, C[u]) inside the 32 entries are dropped, and so
+// is a candidate whose gain is >= 0 even with A_x at its bound k |x|); the
+// entries kept from kChunks chunks are then scored by groups of lanes.  A
+// singleton {u} is scored from the two label rows; another cluster from its
+// summary rows, then (unless the lower bound on dD from the summary is
+// already >= 0, in which case the move can never be proposed) from probes of
+// the open partitions.  A move with dD < 0 bids its packed (dD, C[u]) at
+// best[v] with an atomic minimum (a candidate kept in two chunks bids the
+// same key twice).  All group reductions are outside the branches, so every
+// lane of the warp takes part in every shuffle.
 template <bool kSingle>
 __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
 {
@@ -315,49 +320,54 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
     EdgeScratch& es = sh[w];
     const JobInfo J0 = a.job[0];
     const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
-    for (long long base = ((long long)blockIdx.x * kWarpsPerBlock + w) * 32; base < a.nnz; base += nwarps * 32) {
-        const long long e = base + lane;
-        int v = 0, u = 0, x = -1, j = 0, cv = 0;
-        if (e < a.nnz) {
-            v = __ldg(a.src + e);
-            if (!kSingle) j = __ldg(a.jid + v);
-        }
-        // a chunk whose entries all belong to stopped jobs is skipped whole
-        if (!kSingle && __all_sync(kFull, e >= a.nnz || a.js[j].stop)) continue;
-        if (e < a.nnz) {
-            u = __ldg(a.col + e);
-            if (u != v && (kSingle || !a.js[j].stop)) {
-                x = __ldg(a.C + u);
-                cv = __ldg(a.C + v);
-                if (x == cv) x = -1;
+    constexpr long long span = 32 * kChunks;
+    for (long long base = ((long long)blockIdx.x * kWarpsPerBlock + w) * span; base < a.nnz; base += nwarps * span) {
+        int nf = 0;
+        for (int c = 0; c < kChunks; ++c) {
+            const long long e = base + c * 32 + lane;
+            int v = 0, u = 0, x = -1, j = 0, cv = 0;
+            if (e < a.nnz) {
+                v = __ldg(a.src + e);
+                if (!kSingle) j = __ldg(a.jid + v);
             }
-        }
-        const unsigned long long pair = x >= 0 ? ((unsigned long long)(unsigned)v << 32) | (unsigned)x : kEmpty;
-        const unsigned same = __match_any_sync(kFull, pair);
-        bool keep = x >= 0 && (__ffs(same) - 1) == lane;
-        int sx = 0, sa = 0, Aa = 0;
-        if (keep) {
-            sx = __ldg(a.size + x);
-            sa = __ldg(a.size + cv);
-            Aa = __ldg(a.aown + v);
-            // exact prune: n(x, i, l) <= |x| gives A_x <= k |x|, so a move whose
-            // gain is >= 0 even at that bound is never proposed
-            const long long k = kSingle ? J0.k : a.job[j].k;
-            if (2 * ((long long)Aa - k - k * sx) - k * ((long long)sa - 1 - sx) >= 0) keep = false;
-        }
-        const unsigned km = __ballot_sync(kFull, keep);
-        if (keep) {
-            const int p = __popc(km & lt);
-            es.v[p] = v;
-            es.u[p] = u;
-            es.x[p] = x;
-            if (!kSingle) es.j[p] = j;
-            es.sx[p] = sx;
-            es.sa[p] = sa;
-            es.Aa[p] = Aa;
+            // a chunk whose entries all belong to stopped jobs (or lie past
+            // the end) is skipped whole
+            if (__all_sync(kFull, e >= a.nnz || (!kSingle && a.js[j].stop))) continue;
+            if (e < a.nnz) {
+                u = __ldg(a.col + e);
+                if (u != v && (kSingle || !a.js[j].stop)) {
+                    x = __ldg(a.C + u);
+                    cv = __ldg(a.C + v);
+                    if (x == cv) x = -1;
+                }
+            }
+            const unsigned long long pair = x >= 0 ? ((unsigned long long)(unsigned)v << 32) | (unsigned)x : kEmpty;
+            const unsigned same = __match_any_sync(kFull, pair);
+            bool keep = x >= 0 && (__ffs(same) - 1) == lane;
+            int sx = 0, sa = 0, Aa = 0;
+            if (keep) {
+                sx = __ldg(a.size + x);
+                sa = __ldg(a.size + cv);
+                Aa = __ldg(a.aown + v);
+                // exact prune: n(x, i, l) <= |x| gives A_x <= k |x|, so a move
+                // whose gain is >= 0 even at that bound is never proposed
+                const long long k = kSingle ? J0.k : a.job[j].k;
+                if (2 * ((long long)Aa - k - k * sx) - k * ((long long)sa - 1 - sx) >= 0) keep = false;
+            }
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int p = nf + __popc(km & lt);
+                es.v[p] = v;
+                es.u[p] = u;
+                es.x[p] = x;
+                if (!kSingle) es.j[p] = j;
+                es.sx[p] = sx;
+                es.sa[p] = sa;
+                es.Aa[p] = Aa;
+            }
+            nf += __popc(km);
         }
         __syncwarp();
-        const int nf = __popc(km);
         for (int r0 = 0; r0 < nf; r0 += per) {
             const int q = r0 + lane / gs;
             const bool valid = q < nf;
@@ -368,18 +378,19 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
             const bool single = valid && sx == 1;
             const bool table = valid && sx > 1;
             const int* gv = a.G + row_of(J, valid ? ev : J.vo);
-            int rc = 0, ex = 0, ub = 0;
-            if (single) rc = row_part(a.G + row_of(J, eu), gv, J.kp >> 2, l, gs);
-            if (table) summary_part(a, J, gv, ex_, sx, l, gs, ex, ub);
-            rc = group_sum(rc, gs);
-            ex = group_sum(ex, gs);
+            // part = matching labels with u's row (a singleton) or the exact
+            // summary part (another cluster); ub only for the latter
+            int part = 0, ub = 0;
+            if (single) part = row_part(a.G + row_of(J, eu), gv, J.kp >> 2, l, gs);
+            if (table) summary_part(a, J, gv, ex_, sx, l, gs, part, ub);
+            part = group_sum(part, gs);
             ub = group_sum(ub, gs);
             const bool open = table && 2 * (Aa - k - ub) - k * (sa - 1 - sx) < 0;
             int pb = 0;
             if (open) pb = probe_part(a, J, a.table, mask, gv, ex_, sx, l, gs);
             pb = group_sum(pb, gs);
             if ((single || open) && l == 0) {
-                const int A = single ? rc - (J.kp - k) : ex + pb;
+                const int A = single ? part - (J.kp - k) : part + pb;
                 const int dD = 2 * (Aa - k - A) - k * (sa - 1 - sx);
                 if (dD < 0) atomicMin(&a.best[ev], pack_key(dD, ex_));
             }
