@@ -77,7 +77,14 @@ typedef struct {
                                light path or one vertex's own cluster: 1, 2, 4, 8, 16 or 32;
                                0 = automatic (by the largest k: about 10 partitions per lane).
                                Results do not depend on it; speed does */
-    int32_t reserved[2];    /* must be zero */
+    int32_t active_set;     /* 1: after the first sweep of a run, a vertex whose own cluster and
+                               whose previous bid's target did not change in the previous
+                               sweep scores only its candidates whose cluster changed and
+                               keeps its previous bid if that stays the least (exactly what
+                               scoring every candidate would give).  Results are identical;
+                               it changes how many edges a sweep evaluates.  0 (default):
+                               every sweep scores every edge */
+    int32_t reserved[1];    /* must be zero */
 } cc_options;
 
 /* State of the contingency hash of a context. */

@@ -357,6 +357,7 @@ cc_status check_options(const cc_options& opt, std::string* msg)
     if (opt.sweep_mode < 0 || opt.sweep_mode > 2) return bad(CC_ERR_INVALID, "sweep_mode must be 0, 1 or 2");
     if (opt.lanes < 0 || opt.lanes > 32 || (opt.lanes & (opt.lanes - 1)) != 0)
         return bad(CC_ERR_INVALID, "lanes must be 0 or a power of two up to 32");
+    if (opt.active_set != 0 && opt.active_set != 1) return bad(CC_ERR_INVALID, "active_set must be 0 or 1");
     return CC_OK;
 }
 
@@ -381,6 +382,7 @@ void finish_plan(Plan& p, const cc_options& opt)
         sizeof(JobInfo) * J, sizeof(JobState) * J, 8 * (N + 1), 4 * (size_t)p.nnz, 4 * (size_t)p.nnz,
         4 * N, 4 * (size_t)p.rows, 8 * (size_t)p.rows, 4 * N, 4 * N, 4 * N, 8 * N, 4 * N,
         sizeof(Slot) * (size_t)p.cap_max, 4 * N, 4 * N, 4 * N, 4 * N, N, 4 * N, 4 * N, 4 * (N / 1024 + 2),
+        4 * N, 8 * N, N,
         4 * (3 * N + N / 1024 + 64), sizeof(DevState), sizeof(cc_sweep_info) * J * (size_t)p.hist_cap};
     for (size_t b : per) p.persistent += rounded(b);
     const size_t tmp[] = {8 * (N + J), 8 * (J + 1), 4 * (size_t)p.keys, 8 * (J + 1), 4 * (size_t)p.parts, 4 * J,
@@ -479,6 +481,9 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     CC_TRY(dalloc(c, &c->dsize, (size_t)N));
     CC_TRY(dalloc(c, &c->best, (size_t)N));
     CC_TRY(dalloc(c, &c->aown, (size_t)N));
+    CC_TRY(dalloc(c, &c->chg, (size_t)N));
+    CC_TRY(dalloc(c, &c->prev, (size_t)N));
+    CC_TRY(dalloc(c, &c->act, (size_t)N));
     CC_TRY(dalloc(c, &c->table, (size_t)cap));
     CC_TRY(dalloc(c, &c->pv, (size_t)N));
     CC_TRY(dalloc(c, &c->pa, (size_t)N));
@@ -626,6 +631,10 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     a.keys = (unsigned long long)keys;
     a.sweep_mode = c->opt.sweep_mode;
     a.gs = c->opt.lanes > 0 ? c->opt.lanes : lanes_for_k(kmax);
+    a.active_set = c->opt.active_set;
+    a.chg = c->chg;
+    a.prev = c->prev;
+    a.act = c->act;
     a.pv = c->pv;
     a.pa = c->pa;
     a.pb = c->pb;

@@ -102,6 +102,8 @@ struct DevState {
     int run_limit;               // sweep limit of the current run
     int run_bodies;              // sweeps of the current run that did work (retried ones included)
     unsigned long long region_launches;  // kernels run inside the gated regions of sweep graphs
+    int stamp;                   // number of the current sweep (since creation; retried sweeps reuse it)
+    int all_active;              // 1: every vertex is scored in this sweep (first sweep of a run)
 };
 
 // Arguments of the kernels (passed by value).
@@ -129,6 +131,10 @@ struct SweepArgs {
     unsigned long long keys;     // sum_j k_j n_j: no C has more live keys
     int sweep_mode;              // 0 automatic, 1 always staged deltas, 2 always rebuild
     int gs;                      // lanes that score one item (a power of two, 1..32)
+    int active_set;              // 1: score only the active vertices (cc_options.active_set)
+    int* chg;                   // per cluster id: stamp of the last sweep that moved a vertex into or out of it
+    unsigned long long* prev;   // per vertex: its bid of the last sweep that scored it (kEmpty: none)
+    unsigned char* act;         // per vertex: 1 if all its candidates are scored in this sweep
     int* pv;                    // proposal list: vertex,
     int* pa;                    //   source cluster,
     int* pb;                    //   target cluster,

@@ -41,6 +41,9 @@ struct cc_ctx {
     int* dsize = nullptr;
     unsigned long long* best = nullptr;
     int* aown = nullptr;
+    int* chg = nullptr;                 // active set: change stamp per cluster id (n)
+    unsigned long long* prev = nullptr; // active set: previous bid per vertex (n)
+    unsigned char* act = nullptr;       // active set: scored in this sweep (n)
     ccg::Slot* table = nullptr;
     int* pv = nullptr;
     int* pa = nullptr;

@@ -203,6 +203,9 @@ __global__ void k_init_state(SweepArgs a)
         a.size[v] = 1;
         a.dsize[v] = 0;
         a.best[v] = kEmpty;
+        a.chg[v] = -2;  // stamps start at 0: never "the previous sweep"
+        a.prev[v] = kEmpty;
+        a.act[v] = 1;
     }
 }
 

@@ -76,6 +76,7 @@ __global__ void k_run_begin(SweepArgs a, int limit)
         st->stop = 0;
         st->run_limit = limit;
         st->run_bodies = 0;
+        st->all_active = 1;
     }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.jobs; j += gridDim.x * blockDim.x) {
         a.js[j].stop = 0;
@@ -88,6 +89,7 @@ __global__ void k_begin(SweepArgs a)
     DevState* st = a.st;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->skip = (st->stop || st->err) ? 1 : 0;
+        if (!st->skip) st->stamp += 1;
         st->nprop = 0;
         st->pkeys = 0;
         st->overflow = 0;
@@ -253,7 +255,23 @@ __host__ __device__ __forceinline__ int lanes_per_item(int k)
 // A_a for every vertex of a running job: k for a singleton, else the summary
 // part of its own cluster plus probes of the open partitions.  One group of
 // lanes per vertex.
+// ---- active set ------------------------------------------------------
+// With cc_options.active_set, every move stamps its two clusters with the
+// sweep's number, and a sweep after the first of a run re-scores only what
+// the previous sweep can have changed.  v's gain towards a candidate x
+// depends on A_a and |a| of its own cluster a and on |x| and A_x of x; v's
+// candidates are the clusters of its neighbours, and a neighbour that moves
+// stamps both its clusters.  So:
+//   * A_a (aown[v]) is recomputed only if a was stamped;
+//   * if neither a nor the target of v's previous bid was stamped, the
+//     candidates that were not stamped keep their gains, and v's new bid is
+//     the least of its previous bid and the bids of its stamped candidates:
+//     only those are scored;
+//   * otherwise (act[v] = 1) every candidate of v is scored.
+// The first sweep of a run scores everything.
+
 // kSingle: the context holds one job, so every vertex belongs to job 0 and
+// the job is running whenever the sweep is not skipped.// kSingle: the context holds one job, so every vertex belongs to job 0 and
 // the job is running whenever the sweep is not skipped.
 template <bool kSingle>
 __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
@@ -265,15 +283,28 @@ __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
     const int lane = threadIdx.x & 31, l = lane & (gs - 1);
     const long long groups = (long long)gridDim.x * blockDim.x / gs;
     const JobInfo J0 = a.job[0];
+    const int all = st->all_active, last = st->stamp - 1;
     for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x - lane) / gs; base < a.n;
          base += groups) {
         const long long v = base + lane / gs;
         const bool valid = v < a.n;
         const int j = (kSingle || !valid) ? 0 : __ldg(a.jid + v);
-        const bool on = valid && (kSingle || !a.js[j].stop);
-        if (!kSingle && !__any_sync(kFull, on)) continue;  // vertices of stopped jobs only
+        const bool run = valid && (kSingle || !a.js[j].stop);
+        const int cv = run ? __ldg(a.C + v) : 0;
+        bool on = run;
+        if (a.active_set && !all && run) {
+            // A_a again only if a changed; every candidate again if a or the
+            // previous bid's target changed
+            const bool own = a.chg[cv] == last;
+            const unsigned long long p = a.prev[v];
+            const bool full = own || (p != kEmpty && a.chg[(int)(unsigned)(p & 0xffffffffull)] == last);
+            on = own;
+            if (l == 0) a.act[v] = full ? 1 : 0;
+        } else if (a.active_set && run && l == 0) {
+            a.act[v] = 1;
+        }
+        if (!__any_sync(kFull, on)) continue;  // no vertex to score in this group of the warp
         const JobInfo J = kSingle ? J0 : a.job[j];
-        const int cv = on ? __ldg(a.C + v) : 0;
         const int sa = on ? __ldg(a.size + cv) : 1;
         const int* gv = a.G + row_of(J, on ? v : J.vo);
         int ex = 0, ub = 0, pb = 0;
@@ -319,6 +350,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
     const unsigned lt = (1u << lane) - 1u;
     EdgeScratch& es = sh[w];
     const JobInfo J0 = a.job[0];
+    const int all = st->all_active, last = st->stamp - 1;
     const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
     constexpr long long span = 32 * kChunks;
     for (long long base = ((long long)blockIdx.x * kWarpsPerBlock + w) * span; base < a.nnz; base += nwarps * span) {
@@ -330,15 +362,19 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
                 v = __ldg(a.src + e);
                 if (!kSingle) j = __ldg(a.jid + v);
             }
-            // a chunk whose entries all belong to stopped jobs (or lie past
-            // the end) is skipped whole
-            if (__all_sync(kFull, e >= a.nnz || (!kSingle && a.js[j].stop))) continue;
-            if (e < a.nnz) {
+            // entries of stopped jobs are not scored; a chunk of only such
+            // entries is skipped whole
+            const bool live = e < a.nnz && (kSingle || !a.js[j].stop);
+            if (__all_sync(kFull, !live)) continue;
+            if (live) {
                 u = __ldg(a.col + e);
-                if (u != v && (kSingle || !a.js[j].stop)) {
+                if (u != v) {
                     x = __ldg(a.C + u);
                     cv = __ldg(a.C + v);
                     if (x == cv) x = -1;
+                    // active set: only candidates that changed, unless v is
+                    // scored in full
+                    else if (a.active_set && !all && !a.act[v] && a.chg[x] != last) x = -1;
                 }
             }
             const unsigned long long pair = x >= 0 ? ((unsigned long long)(unsigned)v << 32) | (unsigned)x : kEmpty;
@@ -420,9 +456,17 @@ __global__ void __launch_bounds__(kBlock) k_collect(SweepArgs a)
         __syncthreads();
         const long long v = b0 + threadIdx.x;
         if (v < a.n) {
-            const unsigned long long key = a.best[v];
+            unsigned long long key = a.best[v];
+            if (key != kEmpty) a.best[v] = kEmpty;
+            if (a.active_set) {
+                // a vertex scored only on its changed candidates keeps its
+                // previous bid if that is still the least; a vertex of a
+                // stopped job bids nothing
+                if (a.js[a.jid[v]].stop) key = kEmpty;
+                else if (!st->all_active && !a.act[v] && a.prev[v] < key) key = a.prev[v];
+                a.prev[v] = key;
+            }
             if (key != kEmpty) {
-                a.best[v] = kEmpty;
                 const int job = a.jid[v];
                 acc.add(job, 1);
                 const int p = atomicAdd(&s_cnt, 1);
@@ -516,6 +560,10 @@ __global__ void k_h_apply(SweepArgs a, int undo)
         a.C[v] = undo ? ca : cb;
         atomicAdd(&a.size[ca], undo ? 1 : -1);
         atomicAdd(&a.size[cb], undo ? -1 : 1);
+        if (!undo) {
+            a.chg[ca] = st->stamp;
+            a.chg[cb] = st->stamp;
+        }
     }
 }
 
@@ -832,6 +880,8 @@ __global__ void k_commit(SweepArgs a)
             if (mode == 1 && a.pflag[p]) {
                 if (l == 0) {
                     a.C[v] = cb;
+                    a.chg[ca] = st->stamp;
+                    a.chg[cb] = st->stamp;
                     int d = atomicExch(&a.dsize[ca], 0);
                     if (d) atomicAdd(&a.size[ca], d);
                     d = atomicExch(&a.dsize[cb], 0);
@@ -859,6 +909,8 @@ __global__ void k_commit(SweepArgs a)
                 if (l == 0) {
                     job = j;
                     a.C[v] = cb;
+                    a.chg[ca] = st->stamp;
+                    a.chg[cb] = st->stamp;
                     atomicAdd(&a.size[ca], -1);
                     atomicAdd(&a.size[cb], 1);
                     moved = 1;
@@ -954,8 +1006,10 @@ __global__ void k_end(SweepArgs a)
         st->abort = 1;
         st->rebuild = 1;
         st->retries += 1;
+        st->stamp -= 1;  // the retry is the same sweep: it reuses the stamp
         return;
     }
+    st->all_active = 0;
     st->stop = st->active == 0 ? 1 : 0;
     // compaction: rebuild without the dead keys when occupied slots pass one
     // half of the capacity; the new capacity holds the live keys plus k x

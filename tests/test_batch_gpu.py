@@ -231,3 +231,15 @@ def test_batch_of_one_equals_single(cc):
         assert b.history(0) == s.history()
         np.testing.assert_array_equal(b.cluster_ids(), s.cluster_ids())
         assert b.objective(0) == s.objective() == s.objective_recompute()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_active_set(cc, mode):
+    """A batch with the active set: jobs stop at different sweeps, and a
+    stopped job's vertices never repeat an old bid."""
+    jobs = _special_jobs() + _mixed_jobs(20, 111)
+    refs = [oracle.sync_run(ro, col, lab, 20) for ro, col, lab in jobs]
+    assert len({r.sweeps for r in refs}) > 2
+    with cc.ConsensusBatch(jobs, options(cc, sweep_mode=mode, active_set=1)) as b:
+        assert b.run_until_converged(20) == max(r.sweeps for r in refs)
+        _check_batch(b, jobs, refs)

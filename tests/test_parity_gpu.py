@@ -400,3 +400,59 @@ def test_full_size_lfr_as_benchmarked(cc):
             np.testing.assert_array_equal(job.cluster_ids(), ref.C)
         assert job.objective() == ref.F == job.objective_recompute()
         np.testing.assert_array_equal(job.consensus_labels(), oracle.renumber(ref.C))
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,k,seed", [(20000, 8, 11), (5003, 37, 12), (12000, 64, 14)])
+def test_active_set_runs(cc, n, k, seed, mode):
+    """With the active set, sweeps after the first re-score only the vertices
+    near clusters that changed; the run still equals the oracle's, sweep by
+    sweep, in every sweep mode."""
+    c = make_config("lfr", n=n, k=k, cmin=20, cmax=min(1000, n), max_deg=min(1000, n // 4), seed=seed)
+    ref = oracle.sync_run(c["row_off"], c["col"], c["labels"], 20)
+    assert_same(gpu_run(cc, c["row_off"], c["col"], c["labels"], 20, sweep_mode=mode, active_set=1), ref)
+
+
+def test_active_set_knn_and_reruns(cc):
+    """kNN graph with the active set; a second run on the converged state
+    scores everything in its first sweep and finds nothing; a reset repeats
+    the run exactly."""
+    c = make_config("knn", n=6000, comps=30, dim=20, k=12, seed=21)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    ref = oracle.sync_run(ro, col, lab, 30)
+    with cc.Consensus(ro, col, lab, options(cc, active_set=1)) as job:
+        for _ in range(2):
+            job.reset()
+            assert job.run_until_converged(30) == ref.sweeps
+            assert job.history() == ref.stats
+            np.testing.assert_array_equal(job.cluster_ids(), ref.C)
+        assert job.run_until_converged(30) == 1
+        assert job.history()[-1]["proposals"] == 0
+        assert job.objective() == ref.F == job.objective_recompute()
+
+
+def test_active_set_limited_runs(cc):
+    """Runs of 2 sweeps at a time: each run's first sweep scores everything,
+    later ones only the active set; the trajectory equals the oracle's."""
+    c = make_config("lfr", n=20000, k=8, cmin=20, cmax=1000, max_deg=1000, seed=11)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    ref = oracle.sync_run(ro, col, lab, 20)
+    with cc.Consensus(ro, col, lab, options(cc, active_set=1)) as job:
+        for _ in range(12):
+            job.run_until_converged(2)
+        assert job.history()[: ref.sweeps] == ref.stats
+        np.testing.assert_array_equal(job.cluster_ids(), ref.C)
+
+
+def test_active_set_table_retry(cc):
+    """The retry path (first sweep abandoned for lack of table space) with
+    the active set on."""
+    c = make_config("lfr", n=28000, k=8, cmin=20, cmax=1000, max_deg=500, seed=11)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    ref = oracle.sync_run(ro, col, lab, 20)
+    o = options(cc, table_start_log2=18, sweep_mode=1, active_set=1)
+    with cc.Consensus(ro, col, lab, o) as job:
+        assert job.run_until_converged(20) == ref.sweeps
+        assert job.history() == ref.stats
+        np.testing.assert_array_equal(job.cluster_ids(), ref.C)
+        assert job.table_stats()["retries"] >= 1
