@@ -46,6 +46,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sweep (edges x partitions)/s and % HBM roofline; batched jobs/s, p50/p99 latency"
+
+# DRAM bytes (read + write) of the proposal kernels over one step, from one
+# ncu capture of k_own, k_edges and k_collect on the same workload at
+# n = 500,000, scaled by nnz to the full size; to be taken again whenever
+# those kernels change.
+PROPOSAL_TRAFFIC = {"lfr_n1000000_k20": 4.43e9}
+PROPOSAL_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_own, k_edges, k_collect over "
+                           "one step at n=500000, scaled by nnz (x1.9965)")
 UNIT = "edge-partitions/s"
 
 
@@ -69,6 +77,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32],
                    help="lanes per scored item (0 automatic; identical results)")
+    p.add_argument("--no-regions", action="store_true",
+                   help="plain graph nodes instead of conditional regions (for ncu; identical results)")
     p.add_argument("--sweep-mode", type=int, default=0, choices=[0, 1, 2],
                    help="0 automatic, 1 staged deltas, 2 rebuild (identical results)")
     return p.parse_args()
@@ -524,6 +534,7 @@ def main():
     opts = ccg.cc_default_options()
     opts.sweep_mode = args.sweep_mode
     opts.lanes = args.lanes
+    opts.no_regions = 1 if args.no_regions else 0
     job = ccg.Consensus(ro, col, lab, opts)
     job.set_stream(stream.cuda_stream)
     for _ in range(max(args.warmup, 3)):
@@ -609,6 +620,7 @@ def main():
     opts_a.sweep_mode = args.sweep_mode
     opts_a.lanes = args.lanes
     opts_a.active_set = 1
+    opts_a.no_regions = opts.no_regions
     with ccg.Consensus(ro, col, lab, opts_a) as ja:
         ja.set_stream(stream.cuda_stream)
         for _ in range(3):
@@ -634,6 +646,17 @@ def main():
                       "target did not change scores only its candidates whose cluster changed; fewer edges "
                       "evaluated, identical results"}
 
+    # partition distances of the consensus to each input partition (Methods,
+    # Evaluation metrics), timed on the device, checked against the oracle
+    job.metrics()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    met = job.metrics()
+    met_ms = 1e3 * (time.perf_counter() - t0)
+    metrics = {"ms": met_ms, "what": "Mirkin, split-join, Rand distance and VI to each of the k partitions "
+                                     "(table rebuild + 3 reduction kernels, host-timed, synchronous)",
+               "mean_rand_distance": float(np.mean(met["rand_distance"])), "mean_vi": float(np.mean(met["vi"]))}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, ref = cpu_baseline(c)
@@ -643,6 +666,15 @@ def main():
             cpu["parity"] = "MISMATCH"
         else:
             cpu["parity"] = "bit-exact (labels, every sweep record)"
+        import oracle
+
+        t0 = time.perf_counter()
+        om = oracle.metrics(lab, ref.C)
+        metrics["oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+        metrics["parity"] = ("exact Mirkin and split-join, VI within %.1e" % float(np.max(np.abs(om["vi"] - met["vi"])))
+                             if np.array_equal(om["mirkin"], met["mirkin"]) and np.array_equal(om["split_join"],
+                                                                                                 met["split_join"])
+                             else "MISMATCH")
 
     if rank == 0:
         sw = sweeps_total / args.steps
@@ -664,13 +696,15 @@ def main():
                     "steps": args.e2e_steps, "ms_per_step": 1e3 * e2e_s / args.e2e_steps},
             "roofline": {"kernel": "proposal step (k_own + k_edges + k_collect, one launch each per sweep)",
                          "bound": "hbm", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": PROPOSAL_TRAFFIC.get(c["name"]),
+                         "traffic_source": PROPOSAL_TRAFFIC_SOURCE if c["name"] in PROPOSAL_TRAFFIC else None,
                          "peak_source": peak_src,
                          "algorithmic_bytes_per_step": int(np.sum(balg[:n_sw])),
                          "propose_ms_per_step": prop_total_ms},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "active_set": active,
+            "metrics": metrics,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)

@@ -84,7 +84,11 @@ typedef struct {
                                scoring every candidate would give).  Results are identical;
                                it changes how many edges a sweep evaluates.  0 (default):
                                every sweep scores every edge */
-    int32_t reserved[1];    /* must be zero */
+    int32_t no_regions;     /* 1: capture every kernel of a sweep as a plain node of the sweep
+                               graph (a region a sweep does not need runs kernels that return at
+                               once) instead of behind conditional nodes; for profilers that
+                               cannot see kernels inside graphs with conditional nodes.  Results
+                               are identical.  0 (default): conditional regions */
 } cc_options;
 
 /* State of the contingency hash of a context. */
@@ -175,6 +179,30 @@ typedef struct {
  * cc_objective_recompute need a single-job context (else CC_ERR_INVALID).
  * Errors as cc_create; a message names the first job that failed. */
 cc_status cc_batch_create(int32_t jobs, const cc_job_desc* descs, const cc_options* opt, cc_ctx** out);
+
+/* Distances between a job's consensus and one of its input partitions P_i
+ * (Methods, "Evaluation metrics"; the standard definitions):
+ *   mirkin         Mirkin(C, P_i) over ordered pairs (pairs co-clustered in
+ *                  exactly one of the two); sum_i mirkin = the job's F
+ *   split_join     van Dongen's split-join distance: 2n - sum over clusters
+ *                  c of max_l |c & l| - sum over classes l of P_i of max_c |c & l|
+ *   rand_distance  Rand distance = mirkin / (n (n - 1)), 0 for n = 1
+ *   vi             Meila's variation of information H(C|P_i) + H(P_i|C) in
+ *                  nats, p(c, l) = |c & l| / n (fp64 sums; the order of the
+ *                  sums is not fixed, so the last bits may vary)            */
+typedef struct {
+    int64_t mirkin;
+    int64_t split_join;
+    double rand_distance;
+    double vi;
+} cc_partition_metrics;
+
+/* The distances of every job's current consensus to each of its input
+ * partitions: out (caller-allocated, sum_j k_j entries) receives job 0's k_0
+ * partitions in order, then job 1's, and so on.  Rebuilds the contingency
+ * table at its current capacity first (the results of later sweeps do not
+ * change).  Errors: CC_ERR_OOM (scratch), CC_ERR_CUDA. */
+cc_status cc_metrics(cc_ctx* ctx, cc_partition_metrics* out);
 
 /* Number of jobs of the context (1 for cc_create / cc_create_dev). */
 cc_status cc_job_count(const cc_ctx* ctx, int32_t* out);

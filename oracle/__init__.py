@@ -88,6 +88,9 @@ def _load():
     lib.orc_match.argtypes = [c.c_int32, i32p, i32p, i64p, i32p]
     lib.orc_brute_force.restype = c.c_int64
     lib.orc_brute_force.argtypes = [c.c_int32, c.c_int32, i32p, i32p]
+    f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+    lib.orc_metrics.restype = c.c_int32
+    lib.orc_metrics.argtypes = [c.c_int32, c.c_int32, i32p, i32p, i64p, i64p, f64p]
     _lib = lib
     return lib
 
@@ -116,6 +119,24 @@ def partition_sq(labels) -> int:
     lab = _labels(labels)
     k, n = lab.shape
     return int(_load().orc_partition_sq(n, k, lab))
+
+
+def metrics(labels, C) -> dict:
+    """Distances between C and each input partition (Methods, Evaluation
+    metrics): Mirkin over ordered pairs, Rand distance (Mirkin / n(n-1)),
+    van Dongen's split-join distance, Meila's variation of information (nats)."""
+    lab = _labels(labels)
+    k, n = lab.shape
+    C = np.ascontiguousarray(C, dtype=np.int32)
+    mir = np.zeros(k, np.int64)
+    sj = np.zeros(k, np.int64)
+    vi = np.zeros(k, np.float64)
+    rc = _load().orc_metrics(n, k, lab, C, mir, sj, vi)
+    if rc != 0:
+        raise RuntimeError(f"oracle metrics failed ({rc})")
+    pairs = n * (n - 1)
+    rand = mir / pairs if pairs else np.zeros(k)
+    return {"mirkin": mir, "rand_distance": rand, "split_join": sj, "vi": vi}
 
 
 def mirkin_pairs(X, Y) -> int:

@@ -43,6 +43,7 @@
  * vertices in increasing index, each move evaluated on the current state and
  * applied at once if dD < 0, same candidate set and tie rule.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -560,4 +561,94 @@ int64_t orc_brute_force(int32_t n, int32_t k, const int32_t* labels, int32_t* be
         for (int32_t q = j + 1; q < n; ++q) { rgs[q] = 0; mx[q] = mx[j]; }
     }
     return best;
+}
+
+/* ------------------------------------------------ partition comparison */
+/*
+ * Distances between a partition C and each input partition P_i (Methods,
+ * "Evaluation metrics": the paper compares partitions by the Rand distance,
+ * the split-join distance and the variation of information; it states no
+ * formulas, so the standard definitions are written out here):
+ *   mirkin[i]      Mirkin(C, P_i) over ordered pairs (the Rand distance is
+ *                  mirkin / (n (n - 1)));
+ *   split_join[i]  van Dongen's split-join distance: 2n - sum over clusters c
+ *                  of C of max_l |c & l| - sum over classes l of P_i of
+ *                  max_c |c & l|;
+ *   vi[i]          Meila's variation of information H(C | P_i) + H(P_i | C)
+ *                  in nats, with p(c, l) = |c & l| / n:
+ *                  - sum_{c,l} p(c,l) [log(p(c,l) / p(l)) + log(p(c,l) / p(c))].
+ * The contingency of (C, P_i) comes from sorting the pairs (c, l) of all
+ * vertices; sizes of c and l from sorting C and the labels.
+ */
+static int cmp_u64(const void* a, const void* b)
+{
+    const uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return x < y ? -1 : x > y;
+}
+
+/* Count of x in the sorted array (binary search for the run). */
+static int64_t run_of(const int32_t* arr, int64_t len, int32_t x)
+{
+    return count_sorted(arr, len, x);
+}
+
+int32_t orc_metrics(int32_t n, int32_t k, const int32_t* labels, const int32_t* C, int64_t* mirkin,
+                    int64_t* split_join, double* vi)
+{
+    uint64_t* cl = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));  /* (c, l) pairs */
+    uint64_t* lc = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));  /* (l, c) pairs */
+    int32_t* cs = (int32_t*)malloc((size_t)n * sizeof(int32_t));     /* sorted C */
+    int32_t* ls = (int32_t*)malloc((size_t)n * sizeof(int32_t));     /* sorted labels */
+    if (!cl || !lc || !cs || !ls) { free(cl); free(lc); free(cs); free(ls); return ORC_ERR_NOMEM; }
+    memcpy(cs, C, (size_t)n * sizeof(int32_t));
+    qsort(cs, (size_t)n, sizeof(int32_t), cmp_i32);
+    for (int32_t i = 0; i < k; ++i) {
+        const int32_t* L = labels + (int64_t)i * n;
+        for (int32_t v = 0; v < n; ++v) {
+            /* order-preserving 32-bit images of the two ids */
+            const uint64_t c = (uint32_t)C[v] ^ 0x80000000u, l = (uint32_t)L[v] ^ 0x80000000u;
+            cl[v] = (c << 32) | l;
+            lc[v] = (l << 32) | c;
+            ls[v] = L[v];
+        }
+        qsort(cl, (size_t)n, sizeof(uint64_t), cmp_u64);
+        qsort(lc, (size_t)n, sizeof(uint64_t), cmp_u64);
+        qsort(ls, (size_t)n, sizeof(int32_t), cmp_i32);
+        int64_t sq = 0, max_over_l = 0, max_over_c = 0;
+        double h = 0.0;
+        /* runs of equal (c, l): n(c, l); the best run within each c */
+        for (int64_t a = 0, best = 0; a < n;) {
+            int64_t b = a;
+            while (b < n && cl[b] == cl[a]) ++b;
+            const int64_t ncl = b - a;
+            sq += ncl * ncl;
+            const int32_t c = (int32_t)((uint32_t)(cl[a] >> 32) ^ 0x80000000u);
+            const int32_t l = (int32_t)((uint32_t)cl[a] ^ 0x80000000u);
+            const double p = (double)ncl / n;
+            const double pc = (double)run_of(cs, n, c) / n, pl = (double)run_of(ls, n, l) / n;
+            h -= p * (log(p / pl) + log(p / pc));
+            if (ncl > best) best = ncl;
+            if (b == n || (cl[b] >> 32) != (cl[a] >> 32)) {
+                max_over_l += best;
+                best = 0;
+            }
+            a = b;
+        }
+        /* the best run within each l */
+        for (int64_t a = 0, best = 0; a < n;) {
+            int64_t b = a;
+            while (b < n && lc[b] == lc[a]) ++b;
+            if (b - a > best) best = b - a;
+            if (b == n || (lc[b] >> 32) != (lc[a] >> 32)) {
+                max_over_c += best;
+                best = 0;
+            }
+            a = b;
+        }
+        mirkin[i] = sum_sq_runs(cs, n) + sum_sq_runs(ls, n) - 2 * sq;
+        split_join[i] = 2 * (int64_t)n - max_over_l - max_over_c;
+        vi[i] = h;
+    }
+    free(cl); free(lc); free(cs); free(ls);
+    return ORC_OK;
 }

@@ -68,6 +68,10 @@ class Consensus:
     def objective_recompute(self) -> int:
         return _native.cc_objective_recompute(self._ctx)
 
+    def metrics(self) -> dict:
+        """Mirkin, split-join, Rand and VI distances of the consensus to each input partition."""
+        return _native.cc_metrics(self._ctx, self.k)
+
     def consensus_labels(self) -> np.ndarray:
         return _native.cc_consensus_labels(self._ctx, self.n)
 
@@ -149,6 +153,15 @@ class ConsensusBatch:
 
     def labels(self, job: int) -> np.ndarray:
         return _native.cc_job_labels(self._ctx, job, self.sizes[job])
+
+    def metrics(self) -> list:
+        """Per job, the distances of its consensus to each of its input partitions."""
+        m = _native.cc_metrics(self._ctx, int(sum(self.ks)))
+        out, at = [], 0
+        for k in self.ks:
+            out.append({f: v[at:at + k] for f, v in m.items()})
+            at += k
+        return out
 
     def consensus_labels(self) -> np.ndarray:
         return _native.cc_consensus_labels(self._ctx, self.n)

@@ -24,7 +24,7 @@ EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", 
            "cc_run_until_converged", "cc_last_run_timing", "cc_table_stats", "cc_launch_count", "cc_history", "cc_objective", "cc_objective_recompute",
            "cc_consensus_labels", "cc_cluster_ids", "cc_cluster_ids_dev", "cc_last_error", "cc_destroy",
            "cc_batch_create", "cc_job_count", "cc_job_objective", "cc_job_history", "cc_job_labels",
-           "cc_estimate_bytes", "cc_plan_batches", "cc_server_default_options", "cc_server_create", "cc_server_submit",
+           "cc_metrics", "cc_estimate_bytes", "cc_plan_batches", "cc_server_default_options", "cc_server_create", "cc_server_submit",
            "cc_server_progress", "cc_server_job", "cc_server_stats", "cc_server_last_error", "cc_server_destroy",
            "cc_renumber_noalloc")
 
@@ -42,7 +42,7 @@ class cc_options(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("table_log2", ctypes.c_int32), ("table_start_log2", ctypes.c_int32),
                 ("sweep_mode", ctypes.c_int32), ("lanes", ctypes.c_int32), ("active_set", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("no_regions", ctypes.c_int32)]
 
 
 class cc_table_info(ctypes.Structure):
@@ -59,6 +59,11 @@ class cc_sweep_info(ctypes.Structure):
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class cc_partition_metrics(ctypes.Structure):
+    _fields_ = [("mirkin", ctypes.c_int64), ("split_join", ctypes.c_int64), ("rand_distance", ctypes.c_double),
+                ("vi", ctypes.c_double)]
 
 
 class cc_job_desc(ctypes.Structure):
@@ -136,6 +141,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cc_job_history.argtypes = [P, c.c_int32, c.c_int32, c.POINTER(cc_sweep_info), c.POINTER(c.c_int32)]
     lib.cc_job_labels.restype = c.c_int
     lib.cc_job_labels.argtypes = [P, c.c_int32, P]
+    lib.cc_metrics.restype = c.c_int
+    lib.cc_metrics.argtypes = [P, c.POINTER(cc_partition_metrics)]
     lib.cc_estimate_bytes.restype = c.c_int
     lib.cc_estimate_bytes.argtypes = [c.c_int32, c.POINTER(cc_job_desc), c.POINTER(cc_options),
                                       c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
@@ -376,6 +383,16 @@ def _job_desc(row_off, col, labels, keep):
         raise ValueError("row_off must have n + 1 entries")
     keep += [row_off, col, labels]
     return cc_job_desc(n, len(col), _ptr(row_off).value, _ptr(col).value, k, _ptr(labels).value)
+
+
+def cc_metrics(ctx, parts: int) -> dict:
+    """Distances of the consensus to every input partition (parts = sum of k over jobs):
+    arrays mirkin, split_join (int64), rand_distance, vi (float64), job after job."""
+    buf = (cc_partition_metrics * max(parts, 1))()
+    _check(lib.cc_metrics(ctx, buf), ctx)
+    return {f: np.array([getattr(buf[i], f) for i in range(parts)],
+                        dtype=np.float64 if f in ("rand_distance", "vi") else np.int64)
+            for f, _ in cc_partition_metrics._fields_}
 
 
 def cc_estimate_bytes(sizes, options: cc_options | None = None):

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libcc.so")
-SOURCES = ["setup.cu", "sweep.cu", "api.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["setup.cu", "sweep.cu", "api.cu", "server.cu", "metrics.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -210,7 +210,7 @@ cc_status ensure_graph(cc_ctx* c, int limit, RunGraph** out)
         e = cudaEventRecordWithFlags(g.bound[s], c->own_stream, cudaEventRecordExternal);
         if (e == cudaSuccess)
             e = launch_sweep(c->args, c->rows, c->grid, c->own_stream, g.prop[2 * s], g.prop[2 * s + 1],
-                             c->body_stream);
+                             c->opt.no_regions ? nullptr : c->body_stream);
     }
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(g.bound[limit], c->own_stream, cudaEventRecordExternal);
     cudaStreamCaptureStatus bs = cudaStreamCaptureStatusNone;
@@ -258,7 +258,7 @@ cc_status run(cc_ctx* c, int limit, int* done)
     // so the number of launches is bounded by the limit plus the retries
     for (int launch = 0; launch < limit + 64; ++launch) {
         CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
-        c->launches += (long long)chunk * kKernelsOutsideRegions;
+        c->launches += (long long)chunk * (c->opt.no_regions ? kKernelsPerSweep : kKernelsOutsideRegions);
         r = read_state(c, &st);
         if (r != CC_OK) return r;
         const int ran = st.run_bodies - before;
@@ -350,8 +350,7 @@ cc_status check_options(const cc_options& opt, std::string* msg)
         *msg = m;
         return code;
     };
-    for (int r : opt.reserved)
-        if (r != 0) return bad(CC_ERR_INVALID, "reserved option fields must be zero");
+    if (opt.no_regions != 0 && opt.no_regions != 1) return bad(CC_ERR_INVALID, "no_regions must be 0 or 1");
     if (opt.table_log2 < 0 || opt.table_log2 > 40) return bad(CC_ERR_INVALID, "table_log2 out of range");
     if (opt.table_start_log2 < 0 || opt.table_start_log2 > 40) return bad(CC_ERR_INVALID, "table_start_log2 out of range");
     if (opt.sweep_mode < 0 || opt.sweep_mode > 2) return bad(CC_ERR_INVALID, "sweep_mode must be 0, 1 or 2");
@@ -382,7 +381,7 @@ void finish_plan(Plan& p, const cc_options& opt)
         sizeof(JobInfo) * J, sizeof(JobState) * J, 8 * (N + 1), 4 * (size_t)p.nnz, 4 * (size_t)p.nnz,
         4 * N, 4 * (size_t)p.rows, 8 * (size_t)p.rows, 4 * N, 4 * N, 4 * N, 8 * N, 4 * N,
         sizeof(Slot) * (size_t)p.cap_max, 4 * N, 4 * N, 4 * N, 4 * N, N, 4 * N, 4 * N, 4 * (N / 1024 + 2),
-        4 * N, 8 * N, N,
+        4 * N, 8 * N, N, 4 * J, 8 * (J + 1), 8 * (size_t)p.parts, 8 * (size_t)p.parts,
         4 * (3 * N + N / 1024 + 64), sizeof(DevState), sizeof(cc_sweep_info) * J * (size_t)p.hist_cap};
     for (size_t b : per) p.persistent += rounded(b);
     const size_t tmp[] = {8 * (N + J), 8 * (J + 1), 4 * (size_t)p.keys, 8 * (J + 1), 4 * (size_t)p.parts, 4 * J,
@@ -464,11 +463,20 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
         pfirst[j] = (int)pjob.size();
         for (int i = 0; i < in[j].k; ++i) pjob.push_back(j);
     }
+    c->pfirst = pfirst;
+    c->parts = (int)pjob.size();
+    c->lbase.assign(jobs + 1, 0);
+    for (int j = 0; j < jobs; ++j) c->lbase[j + 1] = c->lbase[j] + ((long long)c->job[j].k << c->job[j].lshift);
+    c->nlabels = c->lbase[jobs];
 
     const unsigned long long cap = plan.cap_max;
     c->cap_max = cap;
 
     CC_TRY(dalloc(c, &c->d_job, (size_t)jobs));
+    CC_TRY(dalloc(c, &c->d_pfirst, (size_t)jobs));
+    CC_TRY(dalloc(c, &c->d_lbase, (size_t)jobs + 1));
+    CC_TRY(dalloc(c, &c->part_sq, (size_t)plan.parts));
+    CC_TRY(dalloc(c, &c->part_slog, (size_t)plan.parts));
     CC_TRY(dalloc(c, &c->js, (size_t)jobs));
     CC_TRY(dalloc(c, &c->off, (size_t)N + 1));
     CC_TRY(dalloc(c, &c->col, (size_t)NNZ));
@@ -497,6 +505,8 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     CC_TRY(dalloc(c, &c->st, 1));
     CC_TRY(dalloc(c, &c->hist, (size_t)jobs * c->hist_cap));
     CC_TRY(cudaMemcpyAsync(c->d_job, c->job.data(), sizeof(JobInfo) * jobs, cudaMemcpyHostToDevice, c->stream));
+    CC_TRY(cudaMemcpyAsync(c->d_lbase, c->lbase.data(), sizeof(long long) * (jobs + 1), cudaMemcpyHostToDevice,
+                           c->stream));
 
     DevState s0;
     std::memset(&s0, 0, sizeof(s0));
@@ -513,7 +523,6 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
         int* labels = nullptr;
         long long* d_lo = nullptr;
         int* d_pjob = nullptr;
-        int* d_pfirst = nullptr;
         void* lmap = nullptr;
         const unsigned long long lcap = plan.lcap;
         std::vector<void*> temp;
@@ -536,7 +545,7 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
         if (e == cudaSuccess) e = tmalloc((void**)&labels, sizeof(int) * (size_t)keys);
         if (e == cudaSuccess) e = tmalloc((void**)&d_lo, sizeof(long long) * (jobs + 1));
         if (e == cudaSuccess) e = tmalloc((void**)&d_pjob, sizeof(int) * pjob.size());
-        if (e == cudaSuccess) e = tmalloc((void**)&d_pfirst, sizeof(int) * jobs);
+        int* d_pfirst = c->d_pfirst;
         if (e == cudaSuccess) e = tmalloc(&lmap, 16 * lcap);
         for (int j = 0; j < jobs && e == cudaSuccess; ++j) {
             const JobInfo& J = c->job[j];
@@ -590,6 +599,10 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
         la.lmask = lcap - 1;
         la.rows = rows;
         la.st = c->st;
+        la.part_sq = c->part_sq;
+        la.part_slog = c->part_slog;
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->part_sq, 0, sizeof(long long) * pjob.size(), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->part_slog, 0, sizeof(double) * pjob.size(), c->stream);
         if (e == cudaSuccess) e = launch_compact_labels(la, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&s, c->st, sizeof(s), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -785,7 +798,7 @@ cc_status launch_chunk(cc_ctx* c)
     cc_status r = ensure_graph(c, chunk, &g);
     if (r != CC_OK) return r;
     CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
-    c->launches += (long long)chunk * kKernelsOutsideRegions;
+    c->launches += (long long)chunk * (c->opt.no_regions ? kKernelsPerSweep : kKernelsOutsideRegions);
     CC_CUDA(c, cudaMemcpyAsync(c->hstate, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
     CC_CUDA(c, cudaEventRecord(c->chunk_done, c->stream));
     c->async_launches += 1;
@@ -1164,6 +1177,78 @@ cc_status cc_job_labels(cc_ctx* c, int32_t job, int32_t* out)
     CC_CUDA(c, cudaMemcpyAsync(out, lab + J.vo, sizeof(int) * (size_t)J.n, cudaMemcpyDeviceToHost, c->stream));
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
     return CC_OK;
+}
+
+cc_status cc_metrics(cc_ctx* c, cc_partition_metrics* out)
+{
+    if (!c || !out) return fail(c, CC_ERR_INVALID, "null argument");
+    // a rebuild at the current capacity makes the summary rows exact maxima
+    DevState pre;
+    cc_status r = read_state(c, &pre);
+    if (r != CC_OK) return r;
+    if (pre.err) return check_device_error(c, pre);
+    CC_CUDA(c, cudaMemcpyAsync(&c->st->new_mask, &pre.mask, sizeof(pre.mask), cudaMemcpyHostToDevice, c->stream));
+    CC_CUDA(c, launch_table_rebuild(c->args, c->rows, false, c->stream));
+    c->launches += kKernelsPerRebuild;
+    const int P = c->parts, J = c->jobs;
+    const size_t bytes = sizeof(int) * (size_t)c->nlabels + (sizeof(long long) * 3 + sizeof(double)) * (size_t)P +
+                         (sizeof(long long) + sizeof(double)) * (size_t)J + 64;
+    unsigned char* buf = nullptr;
+    CC_CUDA(c, c->pool ? cudaMallocFromPoolAsync((void**)&buf, bytes, c->pool, c->stream) : cudaMalloc((void**)&buf, bytes));
+    MetricsArgs m{};
+    long long* sq = reinterpret_cast<long long*>(buf);
+    long long* sjc = sq + P;
+    long long* sjl = sjc + P;
+    long long* csq = sjl + P;
+    double* slog = reinterpret_cast<double*>(csq + J);
+    double* cslog = slog + P;
+    int* lmax = reinterpret_cast<int*>(cslog + J);
+    m.pfirst = c->d_pfirst;
+    m.lbase = c->d_lbase;
+    m.nlabels = c->nlabels;
+    m.lmax = lmax;
+    m.sq = sq;
+    m.slog = slog;
+    m.sjc = sjc;
+    m.sjl = sjl;
+    m.csq = csq;
+    m.cslog = cslog;
+    std::vector<long long> h_sq(P), h_sjc(P), h_sjl(P), h_csq(J), h_psq(P);
+    std::vector<double> h_slog(P), h_cslog(J), h_pslog(P);
+    cudaError_t e = cudaMemsetAsync(buf, 0, bytes, c->stream);
+    if (e == cudaSuccess) e = launch_metrics(c->args, m, P, c->stream);
+    c->launches += 3;
+    auto get = [&](void* dst, const void* src, size_t n) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->stream);
+    };
+    get(h_sq.data(), sq, sizeof(long long) * P);
+    get(h_sjc.data(), sjc, sizeof(long long) * P);
+    get(h_sjl.data(), sjl, sizeof(long long) * P);
+    get(h_csq.data(), csq, sizeof(long long) * J);
+    get(h_slog.data(), slog, sizeof(double) * P);
+    get(h_cslog.data(), cslog, sizeof(double) * J);
+    get(h_psq.data(), c->part_sq, sizeof(long long) * P);
+    get(h_pslog.data(), c->part_slog, sizeof(double) * P);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (c->pool) cudaFreeAsync(buf, c->stream);
+    else cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "metrics");
+    for (int j = 0; j < J; ++j) {
+        const JobInfo& Jb = c->job[j];
+        const double n = (double)Jb.n;
+        for (int i = 0; i < Jb.k; ++i) {
+            const int p = c->pfirst[j] + i;
+            cc_partition_metrics& o = out[p];
+            o.mirkin = h_csq[j] + h_psq[p] - 2 * h_sq[p];
+            o.split_join = 2 * Jb.n - h_sjc[p] - h_sjl[p];
+            o.rand_distance = Jb.n > 1 ? (double)o.mirkin / (n * (n - 1.0)) : 0.0;
+            o.vi = (h_cslog[j] + h_pslog[p] - 2.0 * h_slog[p]) / n;
+        }
+    }
+    DevState s;
+    r = read_state(c, &s);
+    if (r != CC_OK) return r;
+    return check_device_error(c, s);
 }
 
 cc_status cc_job_count(const cc_ctx* c, int32_t* out)

@@ -424,6 +424,8 @@ struct LabelArgs {
     unsigned long long lmask;
     long long rows;             // entries of G
     DevState* st;
+    long long* part_sq;         // per global partition: sum_l |P_il|^2
+    double* part_slog;          // per global partition: sum_l |P_il| log |P_il|
 };
 cudaError_t launch_compact_labels(const LabelArgs& a, cudaStream_t s);
 
@@ -439,6 +441,29 @@ cudaError_t launch_table_rebuild(const SweepArgs& a, long long rows, bool condit
                                  bool eval = false);
 // F of every job from scratch into js[j].recompute (without sum_ij |P_ij|^2).
 cudaError_t launch_objective_recompute(const SweepArgs& a, cudaStream_t s);
+
+// ---- metrics.cu ----
+// Sums for the partition distances of every job's consensus against each of
+// its input partitions, from a freshly rebuilt table (its summary rows hold
+// each (cluster, partition)'s largest overlap).  Per global partition P (job
+// j's partition i is P = pfirst[j] + i): sq[P] = sum n(c,i,l)^2, slog[P] =
+// sum n log n, sjc[P] = sum over clusters c of max_l n(c,i,l), sjl[P] = sum
+// over classes l of max_c n(c,i,l); per job: csq[j] = sum |c|^2, cslog[j] =
+// sum |c| log |c|.  lmax: one int per label id of every job (job j's ids start
+// at lbase[j]); all outputs zeroed by the caller.
+struct MetricsArgs {
+    const int* pfirst;
+    const long long* lbase;
+    long long nlabels;      // entries of lmax
+    int* lmax;
+    long long* sq;
+    double* slog;
+    long long* sjc;
+    long long* sjl;
+    long long* csq;
+    double* cslog;
+};
+cudaError_t launch_metrics(const SweepArgs& a, const MetricsArgs& m, int parts, cudaStream_t s);
 
 // ---- api.cu ----
 // Message reported by cc_last_error(NULL) in this thread.

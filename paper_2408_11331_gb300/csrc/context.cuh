@@ -28,6 +28,14 @@ struct cc_ctx {
     std::vector<ccg::JobInfo> job;      // host copy of the job table
     std::vector<long long> F0;          // objective of each job at the singleton start
     std::vector<long long> psq;         // sum_ij |P_ij|^2 of each job
+    std::vector<int> pfirst;            // first global partition of each job
+    std::vector<long long> lbase;       // first label id of each job in a job-concatenated id space
+    long long nlabels = 0;              // sum_j k_j 2^s_j
+    int parts = 0;                      // sum_j k_j
+    int* d_pfirst = nullptr;
+    long long* d_lbase = nullptr;
+    long long* part_sq = nullptr;       // per global partition: sum_l |P_il|^2
+    double* part_slog = nullptr;        // per global partition: sum_l |P_il| log |P_il|
     ccg::JobInfo* d_job = nullptr;
     ccg::JobState* js = nullptr;
     long long* off = nullptr;

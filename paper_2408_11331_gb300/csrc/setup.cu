@@ -188,7 +188,10 @@ __global__ void k_label_sumsq(LabelArgs a, unsigned long long cap)
     for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < cap; s += stride) {
         if (m[s].key == kEmpty) continue;
         const long long c = m[s].cnt;
-        acc.add(a.pjob[(int)(m[s].key >> 32)], c * c);
+        const int P = (int)(m[s].key >> 32);
+        acc.add(a.pjob[P], c * c);
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.part_sq + P), (unsigned long long)(c * c));
+        atomicAdd(a.part_slog + P, (double)c * log((double)c));
     }
     job_acc_finish(acc, a.jobs);
 }

@@ -43,7 +43,7 @@ def test_exports_every_declared_symbol(native):
 def test_default_options(native):
     o = native.cc_default_options()
     assert o.max_sweeps == 20 and o.debug_checks == 0 and o.table_log2 == 0 and o.table_start_log2 == 0
-    assert o.sweep_mode == 0 and o.lanes == 0 and o.active_set == 0 and list(o.reserved) == [0]
+    assert o.sweep_mode == 0 and o.lanes == 0 and o.active_set == 0 and o.no_regions == 0
 
 
 def _create_status(native, n, nnz, row_off, col, k, labels, opt=None):
@@ -66,7 +66,7 @@ def test_host_validation(native):
     st, msg = _create_status(native, 300_000_000, 0, ok, None, 3, ok)  # 3 k n + k >= 2^31
     assert st == 4 and "2^31" in msg
     opt = native.cc_default_options()
-    opt.reserved[0] = 7
+    opt.no_regions = 7
     assert _create_status(native, 5, 0, ok, None, 1, ok, ctypes.byref(opt))[0] == 1
     opt = native.cc_default_options()
     opt.sweep_mode = 3

@@ -456,3 +456,18 @@ def test_active_set_table_retry(cc):
         assert job.history() == ref.stats
         np.testing.assert_array_equal(job.cluster_ids(), ref.C)
         assert job.table_stats()["retries"] >= 1
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_no_regions_same_results(cc, mode):
+    """Sweep graphs without conditional regions (every kernel a plain node,
+    for profilers) give the same runs; their launch count is 43 kernels per
+    sweep body."""
+    c = make_config("lfr", n=20000, k=8, cmin=20, cmax=1000, max_deg=1000, seed=11)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    ref = oracle.sync_run(ro, col, lab, 20)
+    assert_same(gpu_run(cc, ro, col, lab, 20, sweep_mode=mode, no_regions=1), ref)
+    with cc.Consensus(ro, col, lab, options(cc, no_regions=1, sweep_mode=mode)) as job:
+        base = job.launch_count()
+        done = job.run_until_converged(20)
+        assert job.launch_count() - base == 1 + ((done + 3) // 4) * 4 * 43
