@@ -657,6 +657,15 @@ def main():
                                      "(table rebuild + 3 reduction kernels, host-timed, synchronous)",
                "mean_rand_distance": float(np.mean(met["rand_distance"])), "mean_vi": float(np.mean(met["vi"]))}
 
+    # grouping homogeneous partitions: the k x k distances between the input
+    # partitions (each partition made the consensus in turn, then restored)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pdist = job.partition_distances()
+    grouping = {"ms": 1e3 * (time.perf_counter() - t0),
+                "what": f"{k} x {k} split-join / Mirkin / Rand / VI distances between the input partitions",
+                "split_join_median": float(np.median(pdist["split_join"][np.triu_indices(k, 1)]))}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, ref = cpu_baseline(c)
@@ -671,6 +680,12 @@ def main():
         t0 = time.perf_counter()
         om = oracle.metrics(lab, ref.C)
         metrics["oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        row0 = oracle.metrics(lab, lab[0])
+        grouping["oracle_ms_row0"] = 1e3 * (time.perf_counter() - t0)
+        grouping["oracle_ms_estimate"] = grouping["oracle_ms_row0"] * k
+        grouping["parity_row0"] = "exact" if np.array_equal(row0["split_join"], pdist["split_join"][0]) and \
+            np.array_equal(row0["mirkin"], pdist["mirkin"][0]) else "MISMATCH"
         metrics["parity"] = ("exact Mirkin and split-join, VI within %.1e" % float(np.max(np.abs(om["vi"] - met["vi"])))
                              if np.array_equal(om["mirkin"], met["mirkin"]) and np.array_equal(om["split_join"],
                                                                                                  met["split_join"])
@@ -705,6 +720,7 @@ def main():
             "clocks": clk.summary(),
             "active_set": active,
             "metrics": metrics,
+            "grouping": grouping,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)

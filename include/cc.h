@@ -204,6 +204,24 @@ typedef struct {
  * change).  Errors: CC_ERR_OOM (scratch), CC_ERR_CUDA. */
 cc_status cc_metrics(cc_ctx* ctx, cc_partition_metrics* out);
 
+/* Grouping homogeneous partitions (Methods, "Grouping homogeneous
+ * partitions"): the distances between every pair of the job's input
+ * partitions, out[a * k + i] = distances of P_a to P_i (k x k entries,
+ * caller-allocated; the diagonal is zero).  Each P_a in turn is made the
+ * consensus and measured as by cc_metrics; the context's consensus, objective
+ * and history are restored afterwards.  Single-job contexts only.  Errors as
+ * cc_metrics, CC_ERR_INVALID for a batch. */
+cc_status cc_partition_distances(cc_ctx* ctx, cc_partition_metrics* out);
+
+/* Groups k partitions: the complete graph over them, weighted by
+ * distance[a * k + b] (e.g. the split_join field of cc_partition_distances),
+ * keeps the edges whose weight is not above lambda; its connected components
+ * are the groups.  group_of (int32[k], written) numbers them from 0 in order
+ * of their first partition; *groups (may be NULL) receives their count.
+ * Host only.  Errors: CC_ERR_INVALID. */
+cc_status cc_group_partitions(int32_t k, const int64_t* distance, int64_t lambda, int32_t* group_of,
+                              int32_t* groups);
+
 /* Number of jobs of the context (1 for cc_create / cc_create_dev). */
 cc_status cc_job_count(const cc_ctx* ctx, int32_t* out);
 

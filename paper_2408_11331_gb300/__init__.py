@@ -72,6 +72,10 @@ class Consensus:
         """Mirkin, split-join, Rand and VI distances of the consensus to each input partition."""
         return _native.cc_metrics(self._ctx, self.k)
 
+    def partition_distances(self) -> dict:
+        """k x k distances between the input partitions (the consensus is left as it was)."""
+        return _native.cc_partition_distances(self._ctx, self.k)
+
     def consensus_labels(self) -> np.ndarray:
         return _native.cc_consensus_labels(self._ctx, self.n)
 

@@ -24,7 +24,7 @@ EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", 
            "cc_run_until_converged", "cc_last_run_timing", "cc_table_stats", "cc_launch_count", "cc_history", "cc_objective", "cc_objective_recompute",
            "cc_consensus_labels", "cc_cluster_ids", "cc_cluster_ids_dev", "cc_last_error", "cc_destroy",
            "cc_batch_create", "cc_job_count", "cc_job_objective", "cc_job_history", "cc_job_labels",
-           "cc_metrics", "cc_estimate_bytes", "cc_plan_batches", "cc_server_default_options", "cc_server_create", "cc_server_submit",
+           "cc_metrics", "cc_partition_distances", "cc_group_partitions", "cc_estimate_bytes", "cc_plan_batches", "cc_server_default_options", "cc_server_create", "cc_server_submit",
            "cc_server_progress", "cc_server_job", "cc_server_stats", "cc_server_last_error", "cc_server_destroy",
            "cc_renumber_noalloc")
 
@@ -143,6 +143,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cc_job_labels.argtypes = [P, c.c_int32, P]
     lib.cc_metrics.restype = c.c_int
     lib.cc_metrics.argtypes = [P, c.POINTER(cc_partition_metrics)]
+    lib.cc_partition_distances.restype = c.c_int
+    lib.cc_partition_distances.argtypes = [P, c.POINTER(cc_partition_metrics)]
+    lib.cc_group_partitions.restype = c.c_int
+    lib.cc_group_partitions.argtypes = [c.c_int32, P, c.c_int64, P, c.POINTER(c.c_int32)]
     lib.cc_estimate_bytes.restype = c.c_int
     lib.cc_estimate_bytes.argtypes = [c.c_int32, c.POINTER(cc_job_desc), c.POINTER(cc_options),
                                       c.POINTER(c.c_int64), c.POINTER(c.c_int64)]
@@ -393,6 +397,25 @@ def cc_metrics(ctx, parts: int) -> dict:
     return {f: np.array([getattr(buf[i], f) for i in range(parts)],
                         dtype=np.float64 if f in ("rand_distance", "vi") else np.int64)
             for f, _ in cc_partition_metrics._fields_}
+
+
+def cc_partition_distances(ctx, k: int) -> dict:
+    """k x k distances between the job's input partitions (fields as cc_metrics)."""
+    buf = (cc_partition_metrics * (k * k))()
+    _check(lib.cc_partition_distances(ctx, buf), ctx)
+    return {f: np.array([getattr(buf[i], f) for i in range(k * k)],
+                        dtype=np.float64 if f in ("rand_distance", "vi") else np.int64).reshape(k, k)
+            for f, _ in cc_partition_metrics._fields_}
+
+
+def cc_group_partitions(distance, lam: int):
+    """Connected components of the partitions joined by distance <= lam: (group of each, count)."""
+    d = np.ascontiguousarray(distance, dtype=np.int64)
+    k = d.shape[0]
+    out = np.empty(k, np.int32)
+    ng = ctypes.c_int32(0)
+    _check(lib.cc_group_partitions(k, _ptr(d), int(lam), _ptr(out), ctypes.byref(ng)), None)
+    return out, ng.value
 
 
 def cc_estimate_bytes(sizes, options: cc_options | None = None):

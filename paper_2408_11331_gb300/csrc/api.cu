@@ -1251,6 +1251,73 @@ cc_status cc_metrics(cc_ctx* c, cc_partition_metrics* out)
     return check_device_error(c, s);
 }
 
+cc_status cc_partition_distances(cc_ctx* c, cc_partition_metrics* out)
+{
+    if (!c || !out) return fail(c, CC_ERR_INVALID, "null argument");
+    cc_status r = need_single(c);
+    if (r != CC_OK) return r;
+    const int k = c->job[0].k;
+    const long long n = c->n;
+    DevState pre;
+    r = read_state(c, &pre);
+    if (r != CC_OK) return r;
+    if (pre.err) return check_device_error(c, pre);
+    // the consensus is kept aside and restored; each input partition in turn
+    // becomes the consensus, and the distance reductions give its row
+    int* saved = c->scratch;
+    CC_CUDA(c, cudaMemcpyAsync(saved, c->C, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+    const unsigned long long full = c->cap_max - 1;
+    std::vector<cc_partition_metrics> row(k);
+    for (int a = 0; a < k && r == CC_OK; ++a) {
+        CC_CUDA(c, launch_ids_from_partition(c->args, n, 0, a, c->stream));
+        CC_CUDA(c, launch_state_from_ids(c->args, c->stream));
+        CC_CUDA(c, cudaMemcpyAsync(&c->st->mask, &full, sizeof(full), cudaMemcpyHostToDevice, c->stream));
+        c->launches += 3;
+        r = cc_metrics(c, row.data());
+        for (int i = 0; r == CC_OK && i < k; ++i) out[(size_t)a * k + i] = row[i];
+    }
+    // restore C, its sizes and its table at the capacity it had
+    CC_CUDA(c, cudaMemcpyAsync(c->C, saved, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+    CC_CUDA(c, launch_state_from_ids(c->args, c->stream));
+    CC_CUDA(c, cudaMemcpyAsync(&c->st->new_mask, &pre.mask, sizeof(pre.mask), cudaMemcpyHostToDevice, c->stream));
+    CC_CUDA(c, launch_table_rebuild(c->args, c->rows, false, c->stream));
+    c->launches += 2 + kKernelsPerRebuild;
+    if (r != CC_OK) return r;
+    DevState s;
+    r = read_state(c, &s);
+    if (r != CC_OK) return r;
+    return check_device_error(c, s);
+}
+
+cc_status cc_group_partitions(int32_t k, const int64_t* distance, int64_t lambda, int32_t* group_of,
+                              int32_t* groups)
+{
+    if (k < 1 || !distance || !group_of) return fail(nullptr, CC_ERR_INVALID, "cc_group_partitions needs k >= 1 and arrays");
+    std::vector<int> parent(k);
+    for (int i = 0; i < k; ++i) parent[i] = i;
+    auto root = [&](int x) {
+        while (parent[x] != x) x = parent[x] = parent[parent[x]];
+        return x;
+    };
+    for (int a = 0; a < k; ++a)
+        for (int b = a + 1; b < k; ++b) {
+            // an edge survives unless its weight is above lambda; either triangle counts
+            if (distance[(size_t)a * k + b] <= lambda || distance[(size_t)b * k + a] <= lambda) {
+                const int ra = root(a), rb = root(b);
+                if (ra != rb) parent[ra > rb ? ra : rb] = ra < rb ? ra : rb;
+            }
+        }
+    std::vector<int> id(k, -1);
+    int ng = 0;
+    for (int i = 0; i < k; ++i) {
+        const int ri = root(i);
+        if (id[ri] < 0) id[ri] = ng++;
+        group_of[i] = id[ri];
+    }
+    if (groups) *groups = ng;
+    return CC_OK;
+}
+
 cc_status cc_job_count(const cc_ctx* c, int32_t* out)
 {
     if (!c || !out) return fail(nullptr, CC_ERR_INVALID, "null argument");

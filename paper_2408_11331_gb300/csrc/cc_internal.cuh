@@ -464,6 +464,8 @@ struct MetricsArgs {
     double* cslog;
 };
 cudaError_t launch_metrics(const SweepArgs& a, const MetricsArgs& m, int parts, cudaStream_t s);
+// C of job j's n vertices := its input partition i (cluster id = least vertex of the class).
+cudaError_t launch_ids_from_partition(const SweepArgs& a, long long n, int j, int i, cudaStream_t s);
 
 // ---- api.cu ----
 // Message reported by cc_last_error(NULL) in this thread.

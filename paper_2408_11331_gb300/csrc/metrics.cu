@@ -125,7 +125,24 @@ __global__ void k_met_labels(SweepArgs a, MetricsArgs m)
     }
 }
 
+// C := input partition i of job j as a consensus: every vertex in the cluster
+// named by the least vertex of its class (the representative in its label id).
+__global__ void k_ids_from_partition(SweepArgs a, int j, int i)
+{
+    const JobInfo J = a.job[j];
+    const int mask = (1 << J.lshift) - 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = J.vo + (long long)blockIdx.x * blockDim.x + threadIdx.x; v < J.vo + J.n; v += stride)
+        a.C[v] = (int)(J.vo + (a.G[row_of(J, v) + i] & mask));
+}
+
 }  // namespace
+
+cudaError_t launch_ids_from_partition(const SweepArgs& a, long long n, int j, int i, cudaStream_t s)
+{
+    k_ids_from_partition<<<met_grid(n), kMetBlock, 0, s>>>(a, j, i);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_metrics(const SweepArgs& a, const MetricsArgs& m, int parts, cudaStream_t s)
 {

@@ -214,3 +214,37 @@ def test_plan_batches_host(native):
     assert nb3 == 2  # bins of k: {10, 3, 9, 4, 8}, {60, 50}
     with pytest.raises(native.CCError):
         native.cc_plan_batches([(0, 0, 1)], 1 << 30)
+
+
+def test_group_partitions_host(native):
+    """Components of the threshold graph over partitions (host only)."""
+    d = np.array([[0, 2, 9, 9, 9],
+                  [2, 0, 9, 3, 9],
+                  [9, 9, 0, 9, 9],
+                  [9, 3, 9, 0, 1],
+                  [9, 9, 9, 1, 0]], np.int64)
+    g, n = native.cc_group_partitions(d, 3)
+    assert n == 2 and g.tolist() == [0, 0, 1, 0, 0]
+    g, n = native.cc_group_partitions(d, 2)
+    assert n == 3 and g.tolist() == [0, 0, 1, 2, 2]
+    g, n = native.cc_group_partitions(d, 0)
+    assert n == 5 and g.tolist() == [0, 1, 2, 3, 4]
+    g, n = native.cc_group_partitions(d, 100)
+    assert n == 1 and g.tolist() == [0] * 5
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        k = int(rng.integers(1, 12))
+        m = rng.integers(0, 20, (k, k))
+        m = np.minimum(m, m.T)
+        np.fill_diagonal(m, 0)
+        lam = int(rng.integers(0, 20))
+        g, n = native.cc_group_partitions(m, lam)
+        # same group iff joined by a path of edges <= lam (closure by repeated squaring)
+        adj = (m <= lam).astype(np.int64)
+        reach = adj.copy()
+        for _ in range(k):
+            reach = np.minimum(1, reach + reach @ adj)
+        assert ((g[:, None] == g[None, :]) == (reach > 0)).all()
+        assert n == len(set(g.tolist()))
+    with pytest.raises(native.CCError):
+        native.cc_group_partitions(np.zeros((0, 0), np.int64), 1)

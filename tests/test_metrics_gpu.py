@@ -85,3 +85,47 @@ def test_metrics_batch(cc):
         for j, (ro, col, lab) in enumerate(jobs):
             _same(per_job[j], oracle.metrics(lab, ids[b.offsets[j]:b.offsets[j + 1]]))
             assert int(per_job[j]["mirkin"].sum()) == b.objective(j)
+
+
+def test_partition_distances_and_groups(cc):
+    """Pairwise distances of the input partitions against the oracle, the
+    consensus left untouched, and one consensus per group of homogeneous
+    partitions (Methods, Grouping homogeneous partitions) equal to the
+    oracle's run on that group alone."""
+    rng = np.random.default_rng(12)
+    c = make_config("lfr", n=6000, k=4, cmin=20, cmax=1000, max_deg=500, seed=31)
+    ro, col, lab4 = c["row_off"], c["col"], c["labels"]
+    # two families: the 4 perturbed partitions, and 3 partitions scrambled far from them
+    far = np.stack([rng.permutation(lab4[0]) for _ in range(3)]).astype(np.int32)
+    lab = np.concatenate([lab4, far])
+    k = lab.shape[0]
+    with cc.Consensus(ro, col, lab) as job:
+        job.run_until_converged(20)
+        C, F, hist = job.cluster_ids(), job.objective(), job.history()
+        d = job.partition_distances()
+        np.testing.assert_array_equal(job.cluster_ids(), C)
+        assert job.objective() == F == job.objective_recompute()
+        job.run_until_converged(20)  # continues as if nothing happened: nothing left to move
+        assert job.history()[: len(hist)] == hist and job.history()[-1]["proposals"] == 0
+    for a in range(k):
+        want = oracle.metrics(lab, lab[a])
+        np.testing.assert_array_equal(d["split_join"][a], want["split_join"])
+        np.testing.assert_array_equal(d["mirkin"][a], want["mirkin"])
+        np.testing.assert_allclose(d["vi"][a], want["vi"], rtol=0, atol=VI_TOL)
+    assert (np.diag(d["split_join"]) == 0).all() and (d["split_join"] == d["split_join"].T).all()
+    # a threshold between the within-family and the cross distances
+    within = d["split_join"][:4, :4].max()
+    lam = int(within)
+    groups, ng = cc._native.cc_group_partitions(d["split_join"], lam)
+    assert groups[:4].tolist() == [0] * 4
+    if d["split_join"][:4, 4:].min() > within:
+        assert ng >= 2
+    members = [np.nonzero(groups == g)[0] for g in range(ng)]
+    jobs = [(ro, col, lab[m]) for m in members]
+    with cc.ConsensusBatch(jobs) as b:
+        b.run_until_converged(20)
+        ids = b.cluster_ids()
+        for g, m in enumerate(members):
+            ref = oracle.sync_run(ro, col, lab[m], 20)
+            assert b.history(g) == ref.stats
+            np.testing.assert_array_equal(ids[b.offsets[g]:b.offsets[g + 1]], ref.C)
