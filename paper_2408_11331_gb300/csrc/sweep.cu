@@ -252,9 +252,10 @@ __host__ __device__ __forceinline__ int lanes_per_item(int k)
     return gs;
 }
 
-// A_a for every vertex of a running job: k for a singleton, else the summary
-// part of its own cluster plus probes of the open partitions.  One group of
-// lanes per vertex.
+// A_a for the vertices of running jobs whose cluster changed in the previous
+// sweep (all of them in a run's first sweep): k for a singleton, else the
+// summary part of its own cluster plus probes of the open partitions.  One
+// group of lanes per vertex.
 // ---- active set ------------------------------------------------------
 // With cc_options.active_set, every move stamps its two clusters with the
 // sweep's number, and a sweep after the first of a run re-scores only what
@@ -291,17 +292,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
         const int j = (kSingle || !valid) ? 0 : __ldg(a.jid + v);
         const bool run = valid && (kSingle || !a.js[j].stop);
         const int cv = run ? __ldg(a.C + v) : 0;
-        bool on = run;
-        if (a.active_set && !all && run) {
-            // A_a again only if a changed; every candidate again if a or the
-            // previous bid's target changed
-            const bool own = a.chg[cv] == last;
+        // A_a is a function of v's cluster alone: it is recomputed only when
+        // a vertex moved into or out of that cluster in the previous sweep
+        // (or in a run's first sweep), and kept in aown[] otherwise
+        const bool own = run && (all || a.chg[cv] == last);
+        const bool on = own;
+        if (a.active_set && run && l == 0) {
+            // active set: every candidate again if a or the previous bid's
+            // target changed
             const unsigned long long p = a.prev[v];
             const bool full = own || (p != kEmpty && a.chg[(int)(unsigned)(p & 0xffffffffull)] == last);
-            on = own;
-            if (l == 0) a.act[v] = full ? 1 : 0;
-        } else if (a.active_set && run && l == 0) {
-            a.act[v] = 1;
+            a.act[v] = full ? 1 : 0;
         }
         if (!__any_sync(kFull, on)) continue;  // no vertex to score in this group of the warp
         const JobInfo J = kSingle ? J0 : a.job[j];
