@@ -86,7 +86,6 @@ struct DevState {
     long long live;              // keys with a non-zero count
     unsigned long long mask;     // active table capacity - 1 (a power of two minus one)
     unsigned long long new_mask; // capacity - 1 of a pending rebuild
-    unsigned long long tile_ctr; // work counter of the proposal step
     int skip;                    // 1: this sweep does nothing (every job has stopped)
     int stop;                    // 1: the run has stopped (all jobs)
     int active;                  // jobs still running after the current sweep

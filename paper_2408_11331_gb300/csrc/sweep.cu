@@ -2,22 +2,27 @@
 // job of a context, as a fixed sequence of kernels on one stream so that it
 // can be captured in a CUDA graph:
 //
-//   begin        per-sweep counters (union-wide and per job); the sweep is
-//                skipped once every job has stopped
+//   begin        per-sweep counters (union-wide and per job), the sweep's
+//                stamp; the sweep is skipped once every job has stopped
 //   own/edges/   best move of every vertex against the sweep-start state
 //   collect      (Eq. objective4 with the gain of Eq. objective3): A_a per
-//                vertex, then one lane group per CSR entry bidding its move,
+//                vertex whose cluster changed, then lane groups scoring the
+//                distinct candidates of every 128 CSR entries and bidding,
 //                then the proposal list
 //   route        heavy or light evaluation of the kept moves P1 (results agree)
-//   heavy path   apply P1, rebuild the table, F' - F per job; commit, or undo and
-//                rebuild
-//   light path   singleton guard; stage size and count deltas; exact dF per job
-//   decide       per job: commit P1 if dF < 0, else the matching of P
+//   [heavy path] apply P1, rebuild the table, F' - F per job; commit, or
+//   [rollback]   undo and rebuild
+//   [light path] singleton guard; stage size and count deltas; exact dF per job
 //   bid          matching jobs: drop staged deltas, bid (dD, v) at both clusters
 //   match_keys   winners (least (dD, v) at both ends) insert their target keys
-//   commit       fold staged deltas in (light P1), move the matching winners
+//   commit       fold staged deltas in (light P1), move the matching winners;
+//                every move stamps its two clusters
 //   end          objective, history, stop per job; retry / compaction decisions
-//   rebuild      (conditional) rebuild of the contingency hash
+//   [rebuild]    rebuild of the contingency hash when one is pending
+//
+// The bracketed parts are IF regions of the captured graph, entered only when
+// a one-thread gate kernel finds them needed (all their kernels also check
+// the control block, so a graph without regions gives the same results).
 //
 // Gain of v moving from its cluster a to b (Eq. objective3, u = v excluded),
 // with k the number of partitions of v's job:
@@ -93,7 +98,6 @@ __global__ void k_begin(SweepArgs a)
         st->nprop = 0;
         st->pkeys = 0;
         st->overflow = 0;
-        st->tile_ctr = 0;
         st->heavy = 0;
         st->rollback = 0;
         st->active = 0;
