@@ -1,0 +1,45 @@
+"""bench.py's reference arm runs on the host cores (the oracle), so its JSON
+line can be checked here: one line, with every key of the bench contract."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(*args):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def _check_common(d):
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference"
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_reference_single_job_line():
+    d = _run("--workload", "sbm", "--steps", "2", "--warmup", "1")
+    _check_common(d)
+    assert d["unit"] == "edge-partitions/s" and d["steps"] == 2
+
+
+@pytest.mark.slow
+def test_reference_batch_line():
+    d = _run("--workload", "batch", "--jobs", "8", "--pool", "2")
+    _check_common(d)
+    assert d["unit"] == "jobs/s" and d["config"]["jobs"] == 8
