@@ -359,7 +359,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
     const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
     constexpr long long span = 32 * kChunks;
     for (long long base = ((long long)blockIdx.x * kWarpsPerBlock + w) * span; base < a.nnz; base += nwarps * span) {
-        int nf = 0;
+        // singleton candidates fill the scratch from the front, the others
+        // from the back, so that scoring rounds take one path each
+        int ns = 0, nt = 0;
         for (int c = 0; c < kChunks; ++c) {
             const long long e = base + c * 32 + lane;
             int v = 0, u = 0, x = -1, j = 0, cv = 0;
@@ -395,9 +397,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
                 const long long k = kSingle ? J0.k : a.job[j].k;
                 if (2 * ((long long)Aa - k - k * sx) - k * ((long long)sa - 1 - sx) >= 0) keep = false;
             }
-            const unsigned km = __ballot_sync(kFull, keep);
+            const bool sgl = keep && sx == 1;
+            const unsigned ks = __ballot_sync(kFull, sgl), kt = __ballot_sync(kFull, keep && !sgl);
             if (keep) {
-                const int p = nf + __popc(km & lt);
+                const int p = sgl ? ns + __popc(ks & lt) : (int)span - 1 - (nt + __popc(kt & lt));
                 es.v[p] = v;
                 es.u[p] = u;
                 es.x[p] = x;
@@ -406,12 +409,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
                 es.sa[p] = sa;
                 es.Aa[p] = Aa;
             }
-            nf += __popc(km);
+            ns += __popc(ks);
+            nt += __popc(kt);
         }
         __syncwarp();
+        const int nf = ns + nt;
         for (int r0 = 0; r0 < nf; r0 += per) {
-            const int q = r0 + lane / gs;
-            const bool valid = q < nf;
+            const int qq = r0 + lane / gs;
+            const bool valid = qq < nf;
+            const int q = qq < ns ? qq : (int)span - 1 - (qq - ns);
             const int ev = valid ? es.v[q] : 0, eu = valid ? es.u[q] : 0, ex_ = valid ? es.x[q] : 0;
             const int sx = valid ? es.sx[q] : 0, sa = valid ? es.sa[q] : 0, Aa = valid ? es.Aa[q] : 0;
             const JobInfo J = kSingle ? J0 : a.job[valid ? es.j[q] : 0];
