@@ -25,6 +25,21 @@ def test_hand_worked_example():
     assert m["vi"] == pytest.approx(g["vi"], abs=1e-12)
 
 
+@pytest.mark.parametrize("case", range(2))
+def test_hand_worked_tied_overlaps(case):
+    """Split-join with tied largest overlaps (each tie counts its value once)."""
+    g = json.load(open(os.path.join(GOLDEN, "metrics_ties.json")))["cases"][case]
+    m = _m(g["X"], g["Y"])
+    assert m["mirkin"] == g["mirkin"]
+    assert m["split_join"] == g["split_join"]
+    assert m["rand_distance"] == pytest.approx(g["rand_distance"], abs=1e-15)
+    assert m["vi"] == pytest.approx(g["vi"], abs=1e-12)
+    # the distances are symmetric in X and Y
+    r = _m(g["Y"], g["X"])
+    assert (r["mirkin"], r["split_join"]) == (g["mirkin"], g["split_join"])
+    assert r["vi"] == pytest.approx(g["vi"], abs=1e-12)
+
+
 def _random_partition(rng, n, parts):
     return rng.integers(0, parts, n).astype(np.int32)
 

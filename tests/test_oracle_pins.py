@@ -414,6 +414,42 @@ def test_sequential_trace():
     assert Mt[-1] == 0 or len(Mt) == 20
 
 
+def _seq_golden(g, labels):
+    e = np.array(g["edges"])
+    row_off, col = csr_from_edges(g["n"], e[:, 0], e[:, 1])
+    return oracle.seq_run(row_off, col, np.array(labels, np.int32), 20)
+
+
+def test_golden_sequential_visit_order():
+    """Sequential greedy (Parallel algorithm section, one move at a time):
+    the hand-worked trajectory in increasing vertex order.  A decreasing
+    order ends in another partition, so a reversed visit order fails here."""
+    g = _golden("seq_order_path5.json")
+    assert oracle.objective(np.array(g["labels"], np.int32), oracle.singletons(g["n"])) == g["F0"]
+    C, Ft, Mt = _seq_golden(g, g["labels"])
+    np.testing.assert_array_equal(C, g["increasing"]["C"])
+    assert Ft.tolist() == g["increasing"]["F_trace"]
+    assert Mt.tolist() == g["increasing"]["moves_trace"]
+    assert not np.array_equal(oracle.renumber(np.array(g["decreasing"]["C"])), oracle.renumber(C))
+    # the mirrored instance: its increasing order is the original's decreasing one
+    C, Ft, Mt = _seq_golden(g, g["mirrored_labels"])
+    np.testing.assert_array_equal(C, g["mirrored_increasing"]["C"])
+    assert Ft.tolist() == g["mirrored_increasing"]["F_trace"]
+    mirrored_back = C[::-1]
+    np.testing.assert_array_equal(oracle.renumber(mirrored_back),
+                                  oracle.renumber(np.array(g["decreasing"]["C"])))
+
+
+def test_golden_sequential_tie_rule():
+    """Sequential greedy: a tie between candidate clusters goes to the
+    smaller id (hand-worked on a 3-vertex star)."""
+    g = _golden("seq_tie_star3.json")
+    C, Ft, Mt = _seq_golden(g, g["labels"])
+    np.testing.assert_array_equal(C, g["C"])
+    assert Ft.tolist() == g["F_trace"] and Mt.tolist() == g["moves_trace"]
+    assert not np.array_equal(C, g["tie_to_larger_C"]) and not np.array_equal(C, g["decreasing_C"])
+
+
 def test_identical_copies_recover_partition():
     """P6: k identical copies of P whose clusters induce connected subgraphs ->
     both variants end at C = P with F = 0."""
