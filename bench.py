@@ -1,7 +1,8 @@
 """Benchmark of the consensus sweep on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload lfr|sbm|knn|batch|serve] [--n N] [--k K] [--no-cpu-baseline]
+                    [--workload all|knn|lfr|sbm|batch|serve] [--n N] [--k K]
+                    [--no-cpu-baseline] [--no-extras]
 
 One step = one whole consensus job on resident inputs: reset to the singleton
 start (contingency table rebuilt) and synchronous sweeps until no proposal or
@@ -9,11 +10,18 @@ start (contingency table rebuilt) and synchronous sweeps until no proposal or
 second: nnz * k per sweep that ran, summed over the step, divided by the step
 time (CUDA events on the job's stream).  Prints one JSON line on rank 0.
 
+--workload all (the default): the headline is the largest single-job
+workload that fits one GPU, the kNN-15 graph of a 200-component Gaussian
+mixture in 50-D (n = 2,000,000, k = 50); the same line carries, under "lfr",
+"batch" and "serve", bounded runs of the LFR-style job (n = 1,000,000,
+k = 20), of the batched mix and of the served mix (rank 0, one GPU only).
+
 Multi-GPU: a single job does not shard, so N processes run N independent
 replicas of the job (weak scaling, no collective on the data path).
 
 --impl reference times the CPU oracle (the method written out plainly in C,
-OpenMP over vertices) on the same workload; each step is its first sweep.
+OpenMP over vertices) on the headline workload; each step is its first
+synchronous sweep from the singleton start.
 
 --workload batch: the batched form.  4,096 jobs (n log-uniform in
 [200, 200000], half SBM and half LFR-style, k uniform in [5, 64]) drawn from a
@@ -24,15 +32,16 @@ the same jobs one at a time through cc_create.  Every job's labels are
 compared between the two, and a sample with the oracle.
 
 --workload serve: the served form.  Requests with Poisson arrivals at
-multiples of the one-job-at-a-time service rate, jobs LFR-style (n
-log-uniform in [1000, 2000000], mean degree 10-30, k in [8, 32]) drawn from
-a pool; served by cc_server (continuous batching) and by a one-job-at-a-time
-loop on the same arrivals; p50/p99 latency and jobs/s for each.
+multiples of the server's saturated rate, jobs LFR-style (n log-uniform in
+[1000, 2000000], mean degree 10-30, k in [8, 32]) drawn from a pool; served
+by cc_server (continuous batching) and by a one-job-at-a-time loop on the
+same arrivals; p50/p99 latency and jobs/s for each.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -46,31 +55,29 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sweep (edges x partitions)/s and % HBM roofline; batched jobs/s, p50/p99 latency"
-
-# DRAM bytes (read + write) of the proposal kernels over one step, from one
-# ncu capture of k_own, k_edges and k_collect on the same workload at
-# n = 500,000, scaled by nnz to the full size.  Reported as traffic only
-# while those kernels are the ones captured; k_edges has changed since the
-# last capture (the order in which it scores its candidates), so the value
-# is reported beside, as the last capture's, and traffic is null.
-PROPOSAL_TRAFFIC = {}
-PROPOSAL_TRAFFIC_LAST = {"lfr_n1000000_k20": 4.00e9}
-PROPOSAL_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_own, k_edges, k_collect over "
-                           "one step at n=500000, scaled by nnz (x1.9965); taken before k_edges split its "
-                           "candidates by scoring path")
 UNIT = "edge-partitions/s"
+
+# DRAM bytes (read + write) of the proposal kernels (k_own, k_edges,
+# k_collect) over one step, from ncu captures of those kernels on a smaller
+# case of the same workload, scaled by nnz to the full size; reported as
+# roofline.traffic while the kernels are the ones captured (empty when they
+# changed since).
+PROPOSAL_TRAFFIC = {}
+PROPOSAL_TRAFFIC_SOURCE = {}
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: enough for about 2 s of timed work, at least 10)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["lfr", "sbm", "knn", "batch", "serve"], default="lfr")
+    p.add_argument("--workload", choices=["all", "lfr", "sbm", "knn", "batch", "serve"], default="all")
     p.add_argument("--jobs", type=int, default=None, help="jobs of the batched / served mix (4096 / 20000)")
     p.add_argument("--pool", type=int, default=None, help="distinct generated jobs the mix draws from")
-    p.add_argument("--requests", type=int, default=1000, help="served form: requests per arrival rate")
+    p.add_argument("--requests", type=int, default=None,
+                   help="served form: requests per arrival rate (1000 alone, 400 inside --workload all)")
     p.add_argument("--rates", type=str, default="0.5,0.9,1.5",
                    help="served form: arrival rates as multiples of the server's saturated jobs/s")
     p.add_argument("--budget-frac", type=float, default=0.85, help="share of free device memory for batches")
@@ -78,7 +85,12 @@ def parse():
     p.add_argument("--k", type=int, default=None)
     p.add_argument("--max-sweeps", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=20.0,
+                   help="bound of the oracle's timed sample (sweeps are added while under it)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="warm-up and timed steps only (for profilers): no e2e, active set, metrics, "
+                        "algorithmic bytes, oracle or extra workloads")
     p.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32],
                    help="lanes per scored item (0 automatic; identical results)")
     p.add_argument("--no-regions", action="store_true",
@@ -88,7 +100,7 @@ def parse():
     return p.parse_args()
 
 
-def workload(args, device="cpu"):
+def make_workload(name, args, device="cpu"):
     from workloads import make_config
 
     kw = {}
@@ -96,9 +108,9 @@ def workload(args, device="cpu"):
         kw["n"] = args.n
     if args.k:
         kw["k"] = args.k
-    if args.workload == "knn":
+    if name == "knn":
         kw["device"] = device
-    return make_config(args.workload, **kw)
+    return make_config(name, **kw)
 
 
 def describe(c):
@@ -110,28 +122,31 @@ def describe(c):
     if c["name"].startswith("sbm"):
         return (f"planted-partition SBM n={p['n']} in {p['communities']} communities, p_in={p['p_in']}, "
                 f"p_out={p['p_out']}; k={p['k']} perturbed partitions")
-    return f"kNN-{p['knn']} graph of a {p['comps']}-component Gaussian mixture in {p['dim']}-D, n={p['n']}; k={p['k']}"
+    return (f"symmetrised kNN-{p['knn']} graph of a {p['comps']}-component Gaussian mixture in {p['dim']}-D, "
+            f"n={p['n']}; k={p['k']} partitions at resolutions log-uniform in [50, 2000] plus 10% neighbour relabel")
 
 
 class Clocks:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 50 ms) during the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 50):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            time.sleep(0.3)  # the first sample precedes the timed work
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -166,32 +181,46 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "period_ms": self.period_ms}
 
 
-def algorithmic_bytes(row_off, col, labels, C):
+class ByteModel:
     """Bytes the proposal step must move for one sweep from state C, per the
-    unit costs of the method: CSR offsets and columns, C of each neighbour, the
-    vertex's own label row and cluster, the size of each distinct candidate,
-    and per distinct candidate (own cluster included) either the member's label
-    row (singleton, 4k bytes) or k contingency probes of 12 bytes (8-byte key +
-    4-byte count)."""
-    n = len(C)
-    k = labels.shape[0]
-    nnz = len(col)
-    deg = np.diff(row_off)
-    src = np.repeat(np.arange(n, dtype=np.int64), deg)
-    cu = C[col].astype(np.int64)
-    m = (cu != C[src]) & (col != src)
-    pairs = np.unique(src[m] * n + cu[m])
-    cand = pairs % n
-    size = np.bincount(C, minlength=n)
-    q = len(pairs)
-    single = int((size[cand] == 1).sum())
-    own_multi = int((size[C] > 1).sum())
-    b = 8 * (n + 1) + 4 * nnz + 4 * nnz + 4 * k * n + 8 * n
-    b += 4 * q + single * 4 * k + (q - single) * 12 * k + own_multi * 12 * k
-    return int(b), q
+    unit costs of the method: CSR offsets and columns, C of each neighbour,
+    the vertex's own label row and cluster, the size of each distinct
+    candidate, and per distinct candidate (own cluster included) either the
+    member's label row (singleton, 4k bytes) or k contingency probes of 12
+    bytes (8-byte key + 4-byte count).  Counted with torch on the device
+    (untimed instrumentation)."""
+
+    def __init__(self, torch, row_off, col, k, device):
+        self.torch = torch
+        self.n = len(row_off) - 1
+        self.k = k
+        self.nnz = len(col)
+        deg = torch.from_numpy(np.diff(row_off)).to(device)
+        self.src = torch.repeat_interleave(torch.arange(self.n, device=device), deg)
+        self.col = torch.from_numpy(np.ascontiguousarray(col)).to(device).long()
+        self.device = device
+
+    def __call__(self, C_np):
+        t = self.torch
+        n, k, nnz = self.n, self.k, self.nnz
+        C = t.from_numpy(np.ascontiguousarray(C_np)).to(self.device).long()
+        cu = C[self.col]
+        m = (cu != C[self.src]) & (self.col != self.src)
+        pairs = t.unique(self.src[m] * n + cu[m])
+        cand = pairs % n
+        size = t.bincount(C, minlength=n)
+        q = int(pairs.numel())
+        single = int((size[cand] == 1).sum())
+        own_multi = int((size[C] > 1).sum())
+        b = 8 * (n + 1) + 4 * nnz + 4 * nnz + 4 * k * n + 8 * n
+        b += 4 * q + single * 4 * k + (q - single) * 12 * k + own_multi * 12 * k
+        return int(b), q
+
+    def close(self):
+        del self.src, self.col
 
 
 def run_reference(args, rank, world):
@@ -199,20 +228,22 @@ def run_reference(args, rank, world):
         return
     import oracle
 
-    c = workload(args)
+    name = "knn" if args.workload == "all" else args.workload
+    c = make_workload(name, args, device="cuda" if name == "knn" else "cpu")
     ro, col, lab = c["row_off"], c["col"], c["labels"]
     k, n = lab.shape
     nnz = len(col)
     cores = os.cpu_count() or 1
+    steps = args.steps or 10
     for _ in range(args.warmup):
         oracle.sync_step(ro, col, lab, oracle.singletons(n))
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         oracle.sync_step(ro, col, lab, oracle.singletons(n))
     dt = time.perf_counter() - t0
-    value = nnz * k * args.steps / dt
+    value = nnz * k * steps / dt
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
            "data": "synthetic", "config": {"workload": c["name"], "description": describe(c), "n": n,
                                             "nnz": nnz, "k": k},
@@ -222,18 +253,37 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(c):
-    """The oracle, as it stands, on the same job: the full run to convergence
-    (all host cores via OpenMP)."""
+def cpu_baseline(c, job, budget_s):
+    """The oracle, as it stands, on the same job (all host cores, OpenMP):
+    synchronous sweeps from the singleton start, one at a time, while the
+    time taken stays under budget_s (the whole run if it converges first);
+    then the GPU's run over the same sweeps is compared with it."""
     import oracle
 
     ro, col, lab = c["row_off"], c["col"], c["labels"]
     k, n = lab.shape
-    t0 = time.perf_counter()
-    r = oracle.sync_run(ro, col, lab, 20)
-    dt = time.perf_counter() - t0
-    return {"value": len(col) * k * r.sweeps / dt, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
-            "sample": f"whole job: {r.sweeps} synchronous sweeps from the singleton start ({dt:.1f} s)"}, r
+    C = oracle.singletons(n)
+    F = None
+    stats = []
+    t_total = 0.0
+    while len(stats) < 20:
+        t0 = time.perf_counter()
+        r = oracle.sync_step(ro, col, lab, C, F)
+        t_total += time.perf_counter() - t0
+        stats.append(r.stats)
+        C, F = r.C, r.stats["F"]
+        if r.stats["proposals"] == 0 or t_total > budget_s:
+            break
+    whole = stats[-1]["proposals"] == 0 or len(stats) == 20
+    job.reset()
+    got = [job.sweep() for _ in range(len(stats))]
+    same = got == stats and np.array_equal(job.cluster_ids(), C)
+    what = "whole run" if whole else f"first {len(stats)} sweeps"
+    return {"value": len(col) * k * len(stats) / t_total, "unit": UNIT, "cores": os.cpu_count() or 1,
+            "kind": "oracle", "seconds": round(t_total, 2),
+            "sample": f"{what} of the job: {len(stats)} synchronous sweeps from the singleton start, "
+                      f"each from the previous one's state",
+            "parity": (f"bit-exact ({what}: every sweep record and the raw cluster ids)" if same else "MISMATCH")}, C
 
 
 def over_ranks(dist, seconds, units, device):
@@ -249,12 +299,227 @@ def over_ranks(dist, seconds, units, device):
     return float(mx[0]), float(t[1])
 
 
-def mix_pool(args):
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+    except OSError:
+        p = {}
+    return float(p.get("hbm_gbs", 6800.0)), ("measured" if "hbm_gbs" in p else "fallback")
+
+
+def single_job(args, c, local, dist, rank, world, extras=True):
+    """The single-job workload c: warm-up, K timed steps, then (extras) the
+    algorithmic bytes, e2e through the C ABI, the active set, the distances
+    and the oracle baseline.  Returns the JSON fields of its line."""
+    import torch
+    import paper_2408_11331_gb300 as ccg
+
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    k, n = lab.shape
+    nnz = len(col)
+    stream = torch.cuda.Stream()
+
+    opts = ccg.cc_default_options()
+    opts.sweep_mode = args.sweep_mode
+    opts.lanes = args.lanes
+    opts.no_regions = 1 if args.no_regions else 0
+    job = ccg.Consensus(ro, col, lab, opts)
+    job.set_stream(stream.cuda_stream)
+    warm_ms = []
+    for _ in range(max(args.warmup, 3)):
+        job.reset()
+        job.run_until_converged(args.max_sweeps)
+        warm_ms.append(float(np.sum(job.last_run_timing()[0])))
+    steps = args.steps or max(10, math.ceil(2000.0 / max(min(warm_ms), 1e-3)))
+    launches0 = job.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sweeps_total = 0
+    prop_ms = []
+    sweep_ms = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(steps):
+            job.reset()
+            s = job.run_until_converged(args.max_sweeps)
+            sweeps_total += s
+            a, b = job.last_run_timing()
+            sweep_ms.append(a)
+            prop_ms.append(b)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = job.launch_count() - launches0
+    units = float(nnz) * k * sweeps_total
+    if dist:
+        ms, units = over_ranks(dist, ms, units, "cuda")
+    value = units / (ms / 1e3)
+    sw = sweeps_total / steps
+    per_step_prop = [float(np.sum(p)) for p in prop_ms]
+    prop_total_ms = float(np.mean(per_step_prop))
+    n_sw = len(prop_ms[-1])
+    peak, peak_src = peaks()
+    out = {
+        "value": value, "unit": UNIT, "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / steps,
+        "config": {"workload": c["name"], "description": describe(c), "n": n, "nnz": nnz, "k": k,
+                   "sweeps_per_step": sw, "max_sweeps": args.max_sweeps,
+                   "step": "reset to singletons + synchronous sweeps until no proposal",
+                   "l2": "inputs larger than L2 (CSR + labels + contingency hash > 129 MB), no flush",
+                   "parallelism": f"replicas x{world}",
+                   "timed_s": round(ms / 1e3, 3),
+                   "sweep_ms": [round(float(x), 4) for x in sweep_ms[-1]],
+                   "propose_ms": [round(float(x), 4) for x in prop_ms[-1]]},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if not extras:
+        job.close()
+        return out
+
+    # untimed instrumentation: the start state of every sweep, for the
+    # algorithmic bytes of each proposal launch
+    model = ByteModel(torch, ro, col, k, f"cuda:{local}")
+    job.reset()
+    balg, qs = [], []
+    for _ in range(args.max_sweeps):
+        b, q = model(job.cluster_ids())
+        info = job.sweep()
+        balg.append(b)
+        qs.append(q)
+        if info["proposals"] == 0:
+            break
+    model.close()
+    out["config"]["distinct_candidates_per_sweep"] = qs[:n_sw]
+    achieved = float(np.sum(balg[:n_sw])) / (prop_total_ms / 1e3) / 1e9
+    traffic = PROPOSAL_TRAFFIC.get(c["name"])
+    out["roofline"] = {
+        "kernel": "proposal step (k_own + k_edges + k_collect, one launch each per sweep)",
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": traffic,
+        "achieved_kind": "algorithmic: unit-cost bytes of the method per step / proposal-kernel time",
+        "dram_achieved": (traffic / (prop_total_ms / 1e3) / 1e9) if traffic else None,
+        "dram_frac": (traffic / (prop_total_ms / 1e3) / 1e9 / peak) if traffic else None,
+        "traffic_source": PROPOSAL_TRAFFIC_SOURCE.get(c["name"]),
+        "peak_source": peak_src,
+        "algorithmic_bytes_per_step": int(np.sum(balg[:n_sw])),
+        "propose_ms_per_step": prop_total_ms}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    ro_h, col_h, lab_h = pin(ro), pin(col), pin(lab)
+    out_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    e2e_sweeps = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        j2 = ccg.Consensus(ro_h, col_h, lab_h, opts)
+        e2e_sweeps += j2.run_until_converged(args.max_sweeps)
+        ccg._native.cc_consensus_labels(j2._ctx, n, out_h)
+        j2.close()
+    e2e_s = time.perf_counter() - t0
+    e2e_units = float(nnz) * k * e2e_sweeps
+    if dist:
+        e2e_s, e2e_units = over_ranks(dist, e2e_s, e2e_units, "cuda")
+    out["e2e"] = {"value": e2e_units / e2e_s, "unit": UNIT,
+                  "h2d_bytes_per_step": int(ro.nbytes + col.nbytes + lab.nbytes),
+                  "d2h_bytes_per_step": int(4 * n + 8 * 64),
+                  "steps": args.e2e_steps, "ms_per_step": 1e3 * e2e_s / args.e2e_steps,
+                  "what": "cc_create from pinned host arrays, run to convergence, labels to the host, destroy"}
+
+    # the same job with the active set (cc_options.active_set): sweeps after
+    # the first re-score only vertices near clusters that changed, so fewer
+    # edges are evaluated; reported beside the headline, not in it
+    opts_a = ccg.cc_default_options()
+    opts_a.sweep_mode = args.sweep_mode
+    opts_a.lanes = args.lanes
+    opts_a.active_set = 1
+    opts_a.no_regions = opts.no_regions
+    with ccg.Consensus(ro, col, lab, opts_a) as ja:
+        ja.set_stream(stream.cuda_stream)
+        for _ in range(3):
+            ja.reset()
+            ja.run_until_converged(args.max_sweeps)
+        torch.cuda.synchronize()
+        ev2 = torch.cuda.Event(enable_timing=True)
+        ev3 = torch.cuda.Event(enable_timing=True)
+        reps = min(steps, 10)
+        ev2.record(stream)
+        for _ in range(reps):
+            ja.reset()
+            ja.run_until_converged(args.max_sweeps)
+        ev3.record(stream)
+        torch.cuda.synchronize()
+        ms_a = ev2.elapsed_time(ev3) / reps
+        hist_a = ja.history()
+        sw_a = [round(float(x), 4) for x in ja.last_run_timing()[0]]
+    job.reset()
+    job.run_until_converged(args.max_sweeps)
+    out["active_set"] = {"ms_per_step": ms_a, "speedup": (ms / steps) / ms_a, "sweep_ms": sw_a,
+                         "same_result": hist_a == job.history(),
+                         "note": "cc_options.active_set = 1: after a run's first sweep, a vertex whose cluster and "
+                                 "previous target did not change scores only its candidates whose cluster changed; "
+                                 "fewer edges evaluated, identical results"}
+
+    # partition distances of the consensus to each input partition (Methods,
+    # Evaluation metrics), timed on the host around a synchronous call
+    job.metrics()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    met = job.metrics()
+    metrics = {"ms": 1e3 * (time.perf_counter() - t0),
+               "what": "Mirkin, split-join, Rand distance and VI to each of the k partitions "
+                       "(table rebuild + 3 reduction kernels, host-timed, synchronous)",
+               "mean_rand_distance": float(np.mean(met["rand_distance"])), "mean_vi": float(np.mean(met["vi"]))}
+
+    # grouping homogeneous partitions: the k x k distances between the input
+    # partitions (each partition made the consensus in turn, then restored)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pdist = job.partition_distances()
+    grouping = {"ms": 1e3 * (time.perf_counter() - t0),
+                "what": f"{k} x {k} split-join / Mirkin / Rand / VI distances between the input partitions",
+                "split_join_median": float(np.median(pdist["split_join"][np.triu_indices(k, 1)]))}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        cpu, _ = cpu_baseline(c, job, args.cpu_seconds)
+        job.reset()
+        job.run_until_converged(args.max_sweeps)
+        C_gpu = job.cluster_ids()
+        t0 = time.perf_counter()
+        om = oracle.metrics(lab, C_gpu)
+        metrics["oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        row0 = oracle.metrics(lab, lab[0])
+        grouping["oracle_ms_row0"] = 1e3 * (time.perf_counter() - t0)
+        grouping["oracle_ms_estimate"] = grouping["oracle_ms_row0"] * k
+        grouping["parity_row0"] = "exact" if np.array_equal(row0["split_join"], pdist["split_join"][0]) and \
+            np.array_equal(row0["mirkin"], pdist["mirkin"][0]) else "MISMATCH"
+        metrics["parity"] = ("exact Mirkin and split-join, VI within %.1e" % float(np.max(np.abs(om["vi"] - met["vi"])))
+                             if np.array_equal(om["mirkin"], met["mirkin"]) and np.array_equal(om["split_join"],
+                                                                                                 met["split_join"])
+                             else "MISMATCH")
+    out["metrics"] = metrics
+    out["grouping"] = grouping
+    out["cpu_baseline"] = cpu
+    job.close()
+    return out
+
+
+def mix_pool(args, kind):
     """Specs of the batched / served mix, the pool job each spec draws, and the pool."""
     from workloads.configs import batch_job_specs, serve_job_specs
     from workloads.pool import generate, quantile_pool
 
-    if args.workload == "batch":
+    if kind == "batch":
         specs = batch_job_specs(args.jobs or 4096)
         rep, member = quantile_pool([s[0] for s in specs], args.pool or 256)
         gen = [(specs[r][0], specs[r][1], specs[r][2], None, specs[r][3]) for r in rep]
@@ -267,15 +532,15 @@ def mix_pool(args):
     return specs, member, pool, time.perf_counter() - t0
 
 
-def mix_config(args, specs, member, pool, gen_s):
+def mix_config(kind, specs, member, pool, gen_s):
     ns = np.array([len(pool[m][0]) - 1 for m in member])
-    return {"workload": f"{args.workload}_mix_{len(specs)}", "jobs": len(specs), "pool_distinct_jobs": len(pool),
+    return {"workload": f"{kind}_mix_{len(specs)}", "jobs": len(specs), "pool_distinct_jobs": len(pool),
             "sum_n": int(ns.sum()), "median_n": float(np.median(ns)),
             "draw": "specs sorted by n, cut into equal-count groups; each group's middle spec generated once",
             "generation_s": round(gen_s, 1)}
 
 
-def run_batch(args, rank, world, local, specs, member, pool, gen_s):
+def run_batch(args, world, local, specs, member, pool, gen_s):
     import torch
 
     torch.cuda.set_device(local)
@@ -325,16 +590,14 @@ def run_batch(args, rank, world, local, specs, member, pool, gen_s):
             b.consensus_labels()
         with ccg.Consensus(*jobs[small[0]], opts) as c:
             c.run_until_converged(args.max_sweeps)
-    steps = max(1, args.steps)
+    steps = 1
     got = {}
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         t0 = time.perf_counter()
-        dev_ms = 0.0
-        for s_ in range(steps):
-            dev_ms += batched(got if s_ == 0 else None)
+        dev_ms = batched(got)
         torch.cuda.synchronize()
-        tb = (time.perf_counter() - t0) / steps
+        tb = time.perf_counter() - t0
     ref = {}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -352,29 +615,28 @@ def run_batch(args, rank, world, local, specs, member, pool, gen_s):
         ro, col, lab = pool[i]
         r = oracle.sync_run(ro, col, lab, args.max_sweeps)
         ok_oracle &= bool(np.array_equal(got[first[i]], oracle.renumber(r.C)))
-    cfg = mix_config(args, specs, member, pool, gen_s)
+    cfg = mix_config("batch", specs, member, pool, gen_s)
     cfg.update({"batches": nb, "jobs_per_batch": [len(w) for w in waves], "budget_bytes": budget,
                 "planner": "cc_plan_batches: lane bins of k, then batches within the device budget",
                 "options": "active_set = 1 in both arms",
                 "l2": "inputs larger than L2, no flush"})
-    out = {"metric": "batched jobs/s", "value": J / tb, "unit": "jobs/s", "n_gpus": world, "steps": steps,
-           "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
-           "e2e": {"value": J / tb, "unit": "jobs/s", "h2d_bytes_per_step": int(sum(
-               a.nbytes for ro, col, lab in jobs for a in (ro, col, lab))), "d2h_bytes_per_step": int(4 * sum(
-               s_[0] for s_ in sizes))},
-           "device_ms_per_step": dev_ms / steps,
-           "edge_partitions_per_s": units / tb,
-           "plain_loop": {"value": J / tp, "unit": "jobs/s", "ms": 1e3 * tp,
-                          "how": "each job alone: cc_create, run, labels, destroy"},
-           "speedup_vs_plain_loop": tp / tb,
-           "parity": ("bit-exact per job vs one-at-a-time" if same else "MISMATCH") +
-                     ("; oracle sample bit-exact" if ok_oracle else "; oracle sample MISMATCH"),
-           "clocks": clk.summary()}
-    print(json.dumps(out), flush=True)
+    return {"metric": "batched jobs/s", "value": J / tb, "unit": "jobs/s", "n_gpus": world, "steps": steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
+            "e2e": {"value": J / tb, "unit": "jobs/s", "h2d_bytes_per_step": int(sum(
+                a.nbytes for ro, col, lab in jobs for a in (ro, col, lab))), "d2h_bytes_per_step": int(4 * sum(
+                    s_[0] for s_ in sizes))},
+            "device_ms_per_step": dev_ms,
+            "edge_partitions_per_s": units / tb,
+            "plain_loop": {"value": J / tp, "unit": "jobs/s", "ms": 1e3 * tp,
+                           "how": "each job alone: cc_create, run, labels, destroy"},
+            "speedup_vs_plain_loop": tp / tb,
+            "parity": ("bit-exact per job vs one-at-a-time" if same else "MISMATCH") +
+                      ("; oracle sample bit-exact" if ok_oracle else "; oracle sample MISMATCH"),
+            "clocks": clk.summary()}
 
 
-def run_serve(args, rank, world, local, specs, member, pool, gen_s):
+def run_serve(args, world, local, specs, member, pool, gen_s, requests):
     import torch
 
     torch.cuda.set_device(local)
@@ -383,7 +645,7 @@ def run_serve(args, rank, world, local, specs, member, pool, gen_s):
 
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
     pool = [tuple(pin(a) for a in job) for job in pool]
-    R = min(args.requests, len(member))
+    R = min(requests, len(member))
     req = [int(m) for m in member[:R]]
     opts = ccg.cc_default_options()
     opts.active_set = 1  # jobs/s: re-score only the active set (identical results)
@@ -459,22 +721,21 @@ def run_serve(args, rank, world, local, specs, member, pool, gen_s):
                 "plain": {"jobs_per_s": R / pspan, "p50_ms": 1e3 * float(np.percentile(plat, 50)),
                           "p99_ms": 1e3 * float(np.percentile(plat, 99))}})
     top = results[-1]
-    cfg = mix_config(args, specs, member[:R], pool, gen_s)
+    cfg = mix_config("serve", specs, member[:R], pool, gen_s)
     cfg.update({"requests_per_rate": R, "arrivals": "Poisson, seeds 0x5EED + 4 + rate index",
                 "plain_service_rate_jobs_per_s": mu, "server_saturated_jobs_per_s": sat,
                 "rates": "0.5, 0.9, 1.5 x the server's saturated jobs/s (all requests waiting at t = 0)",
                 "server": "cc_server max_active 8, max_batch_jobs 256",
                 "options": "active_set = 1 in both arms"})
-    out = {"metric": "served jobs/s, p50/p99 latency", "value": top["served"]["jobs_per_s"], "unit": "jobs/s",
-           "n_gpus": world, "steps": len(rates), "warmup": 1, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg, "rates": results,
-           "parity": "bit-exact per request vs the job alone" if sat_bad == 0 and all(
-               r["served"]["mismatches"] == 0 for r in results) else "MISMATCH",
-           "clocks": clk.summary()}
-    print(json.dumps(out), flush=True)
+    return {"metric": "served jobs/s, p50/p99 latency", "value": top["served"]["jobs_per_s"], "unit": "jobs/s",
+            "n_gpus": world, "steps": len(rates), "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg, "rates": results,
+            "parity": "bit-exact per request vs the job alone" if sat_bad == 0 and all(
+                r["served"]["mismatches"] == 0 for r in results) else "MISMATCH",
+            "clocks": clk.summary()}
 
 
-def run_mix_reference(args, rank, specs, member, pool, gen_s):
+def run_mix_reference(args, rank, kind, specs, member, pool, gen_s):
     """The oracle on the mix's jobs in order, for a bounded time (about 20 s)."""
     if rank != 0:
         return
@@ -482,18 +743,16 @@ def run_mix_reference(args, rank, specs, member, pool, gen_s):
 
     t0 = time.perf_counter()
     done = 0
-    units = 0.0
     for m in member:
         ro, col, lab = pool[m]
-        r = oracle.sync_run(ro, col, lab, args.max_sweeps)
+        oracle.sync_run(ro, col, lab, args.max_sweeps)
         done += 1
-        units += float(len(col)) * lab.shape[0] * r.sweeps
         if time.perf_counter() - t0 > 20.0:
             break
     dt = time.perf_counter() - t0
-    cfg = mix_config(args, specs, member, pool, gen_s)
+    cfg = mix_config(kind, specs, member, pool, gen_s)
     unit = "jobs/s"
-    out = {"impl": "reference", "metric": "batched jobs/s" if args.workload == "batch" else "served jobs/s, p50/p99 latency",
+    out = {"impl": "reference", "metric": "batched jobs/s" if kind == "batch" else "served jobs/s, p50/p99 latency",
            "value": done / dt, "unit": unit, "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * dt,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
            "config": cfg,
@@ -503,19 +762,35 @@ def run_mix_reference(args, rank, specs, member, pool, gen_s):
     print(json.dumps(out), flush=True)
 
 
+def compact(part):
+    """The summary of an extra single-job workload kept in the headline line."""
+    keep = ("value", "unit", "ms_per_step", "steps", "roofline", "e2e", "cpu_baseline", "active_set", "clocks",
+            "gpu_launches")
+    d = {key: part.get(key) for key in keep}
+    d["workload"] = part["config"]["workload"]
+    d["description"] = part["config"]["description"]
+    d["config"] = {key: part["config"][key] for key in ("n", "nnz", "k", "sweeps_per_step", "sweep_ms",
+                                                          "propose_ms") if key in part["config"]}
+    return d
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.workload in ("batch", "serve"):
-        if args.impl == "reference" and rank != 0:
+        if rank != 0:
             return
-        specs, member, pool, gen_s = mix_pool(args)
+        specs, member, pool, gen_s = mix_pool(args, args.workload)
         if args.impl == "reference":
-            return run_mix_reference(args, rank, specs, member, pool, gen_s)
-        run = run_batch if args.workload == "batch" else run_serve
-        return run(args, rank, world, local, specs, member, pool, gen_s)
+            return run_mix_reference(args, rank, args.workload, specs, member, pool, gen_s)
+        if args.workload == "batch":
+            out = run_batch(args, world, local, specs, member, pool, gen_s)
+        else:
+            out = run_serve(args, world, local, specs, member, pool, gen_s, args.requests or 1000)
+        print(json.dumps(out), flush=True)
+        return
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -527,209 +802,28 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    import paper_2408_11331_gb300 as ccg
+    import paper_2408_11331_gb300  # noqa: F401  (fails loudly without libcc.so)
 
-    c = workload(args, device=f"cuda:{local}")
-    ro, col, lab = c["row_off"], c["col"], c["labels"]
-    k, n = lab.shape
-    nnz = len(col)
-    stream = torch.cuda.Stream()
-
-    opts = ccg.cc_default_options()
-    opts.sweep_mode = args.sweep_mode
-    opts.lanes = args.lanes
-    opts.no_regions = 1 if args.no_regions else 0
-    job = ccg.Consensus(ro, col, lab, opts)
-    job.set_stream(stream.cuda_stream)
-    for _ in range(max(args.warmup, 3)):
-        job.reset()
-        job.run_until_converged(args.max_sweeps)
-    launches0 = job.launch_count()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    sweeps_total = 0
-    prop_ms = []
-    sweep_ms = []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            job.reset()
-            s = job.run_until_converged(args.max_sweeps)
-            sweeps_total += s
-            a, b = job.last_run_timing()
-            sweep_ms.append(a)
-            prop_ms.append(b)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    launches = job.launch_count() - launches0
-    units = float(nnz) * k * sweeps_total
-    if dist:
-        ms, units = over_ranks(dist, ms, units, "cuda")
-    value = units / (ms / 1e3)
-
-    # untimed instrumentation: the start state of every sweep, for the
-    # algorithmic bytes of each proposal launch
-    job.reset()
-    balg = []
-    qs = []
-    C = job.cluster_ids()
-    for _ in range(args.max_sweeps):
-        b, q = algorithmic_bytes(ro, col, lab, C)
-        info = job.sweep()
-        balg.append(b)
-        qs.append(q)
-        C = job.cluster_ids()
-        if info["proposals"] == 0:
-            break
-    per_step_prop = [float(np.sum(p)) for p in prop_ms]
-    prop_total_ms = float(np.mean(per_step_prop))
-    n_sw = len(prop_ms[-1])
-    achieved = float(np.sum(balg[:n_sw])) / (prop_total_ms / 1e3) / 1e9
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-
-    # end to end through the C ABI with host buffers (pinned), copies inside
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
-    ro_h, col_h, lab_h = pin(ro), pin(col), pin(lab)
-    out_h = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
-    e2e_sweeps = 0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        j2 = ccg.Consensus(ro_h, col_h, lab_h, opts)
-        e2e_sweeps += j2.run_until_converged(args.max_sweeps)
-        ccg._native.cc_consensus_labels(j2._ctx, n, out_h)
-        j2.close()
-    e2e_s = time.perf_counter() - t0
-    e2e_units = float(nnz) * k * e2e_sweeps
-    if dist:
-        e2e_s, e2e_units = over_ranks(dist, e2e_s, e2e_units, "cuda")
-
-    # the same job with the active set (cc_options.active_set): sweeps after
-    # the first re-score only vertices near clusters that changed, so fewer
-    # edges are evaluated; reported beside the headline, not in it
-    opts_a = ccg.cc_default_options()
-    opts_a.sweep_mode = args.sweep_mode
-    opts_a.lanes = args.lanes
-    opts_a.active_set = 1
-    opts_a.no_regions = opts.no_regions
-    with ccg.Consensus(ro, col, lab, opts_a) as ja:
-        ja.set_stream(stream.cuda_stream)
-        for _ in range(3):
-            ja.reset()
-            ja.run_until_converged(args.max_sweeps)
-        torch.cuda.synchronize()
-        ev2 = torch.cuda.Event(enable_timing=True)
-        ev3 = torch.cuda.Event(enable_timing=True)
-        ev2.record(stream)
-        for _ in range(args.steps):
-            ja.reset()
-            ja.run_until_converged(args.max_sweeps)
-        ev3.record(stream)
-        torch.cuda.synchronize()
-        ms_a = ev2.elapsed_time(ev3) / args.steps
-        hist_a = ja.history()
-        sw_a = [round(float(x), 4) for x in ja.last_run_timing()[0]]
-    job.reset()
-    job.run_until_converged(args.max_sweeps)
-    active = {"ms_per_step": ms_a, "speedup": (ms / args.steps) / ms_a, "sweep_ms": sw_a,
-              "same_result": hist_a == job.history(),
-              "note": "cc_options.active_set = 1: after a run's first sweep, a vertex whose cluster and previous "
-                      "target did not change scores only its candidates whose cluster changed; fewer edges "
-                      "evaluated, identical results"}
-
-    # partition distances of the consensus to each input partition (Methods,
-    # Evaluation metrics), timed on the device, checked against the oracle
-    job.metrics()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    met = job.metrics()
-    met_ms = 1e3 * (time.perf_counter() - t0)
-    metrics = {"ms": met_ms, "what": "Mirkin, split-join, Rand distance and VI to each of the k partitions "
-                                     "(table rebuild + 3 reduction kernels, host-timed, synchronous)",
-               "mean_rand_distance": float(np.mean(met["rand_distance"])), "mean_vi": float(np.mean(met["vi"]))}
-
-    # grouping homogeneous partitions: the k x k distances between the input
-    # partitions (each partition made the consensus in turn, then restored)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    pdist = job.partition_distances()
-    grouping = {"ms": 1e3 * (time.perf_counter() - t0),
-                "what": f"{k} x {k} split-join / Mirkin / Rand / VI distances between the input partitions",
-                "split_join_median": float(np.median(pdist["split_join"][np.triu_indices(k, 1)]))}
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu, ref = cpu_baseline(c)
-        job.reset()
-        job.run_until_converged(args.max_sweeps)
-        if job.history() != ref.stats or not np.array_equal(job.cluster_ids(), ref.C):
-            cpu["parity"] = "MISMATCH"
-        else:
-            cpu["parity"] = "bit-exact (labels, every sweep record)"
-        import oracle
-
-        t0 = time.perf_counter()
-        om = oracle.metrics(lab, ref.C)
-        metrics["oracle_ms"] = 1e3 * (time.perf_counter() - t0)
-        t0 = time.perf_counter()
-        row0 = oracle.metrics(lab, lab[0])
-        grouping["oracle_ms_row0"] = 1e3 * (time.perf_counter() - t0)
-        grouping["oracle_ms_estimate"] = grouping["oracle_ms_row0"] * k
-        grouping["parity_row0"] = "exact" if np.array_equal(row0["split_join"], pdist["split_join"][0]) and \
-            np.array_equal(row0["mirkin"], pdist["mirkin"][0]) else "MISMATCH"
-        metrics["parity"] = ("exact Mirkin and split-join, VI within %.1e" % float(np.max(np.abs(om["vi"] - met["vi"])))
-                             if np.array_equal(om["mirkin"], met["mirkin"]) and np.array_equal(om["split_join"],
-                                                                                                 met["split_join"])
-                             else "MISMATCH")
-
+    name = "knn" if args.workload == "all" else args.workload
+    extras = not args.no_extras
+    c = make_workload(name, args, device=f"cuda:{local}")
+    head = single_job(args, c, local, dist, rank, world, extras=extras)
+    del c
+    line = {"metric": METRIC, "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic"}
+    line.update(head)
+    if args.workload == "all" and extras and world == 1 and rank == 0:
+        c = make_workload("lfr", argparse.Namespace(n=None, k=None))
+        line["lfr"] = compact(single_job(args, c, local, None, rank, world))
+        del c
+        specs, member, pool, gen_s = mix_pool(args, "batch")
+        line["batch"] = run_batch(args, world, local, specs, member, pool, gen_s)
+        del pool
+        specs, member, pool, gen_s = mix_pool(args, "serve")
+        line["serve"] = run_serve(args, world, local, specs, member, pool, gen_s, args.requests or 400)
+        del pool
     if rank == 0:
-        sw = sweeps_total / args.steps
-        out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": c["name"], "description": describe(c), "n": n, "nnz": nnz, "k": k,
-                       "sweeps_per_step": sw, "max_sweeps": args.max_sweeps,
-                       "step": "reset to singletons + synchronous sweeps until no proposal",
-                       "l2": "inputs larger than L2 (CSR + labels + contingency hash > 129 MB), no flush",
-                       "parallelism": f"replicas x{world}",
-                       "sweep_ms": [round(float(x), 4) for x in sweep_ms[-1]],
-                       "propose_ms": [round(float(x), 4) for x in prop_ms[-1]],
-                       "distinct_candidates_per_sweep": qs[:n_sw]},
-            "e2e": {"value": e2e_units / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": int(ro.nbytes + col.nbytes + lab.nbytes),
-                    "d2h_bytes_per_step": int(4 * n + 8 * 64),
-                    "steps": args.e2e_steps, "ms_per_step": 1e3 * e2e_s / args.e2e_steps},
-            "roofline": {"kernel": "proposal step (k_own + k_edges + k_collect, one launch each per sweep)",
-                         "bound": "hbm", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": PROPOSAL_TRAFFIC.get(c["name"]),
-                         "traffic_last_capture": PROPOSAL_TRAFFIC_LAST.get(c["name"]),
-                         "traffic_source": PROPOSAL_TRAFFIC_SOURCE if c["name"] in PROPOSAL_TRAFFIC_LAST else None,
-                         "peak_source": peak_src,
-                         "algorithmic_bytes_per_step": int(np.sum(balg[:n_sw])),
-                         "propose_ms_per_step": prop_total_ms},
-            "gpu_launches": int(launches),
-            "clocks": clk.summary(),
-            "active_set": active,
-            "metrics": metrics,
-            "grouping": grouping,
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(out), flush=True)
-    job.close()
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 

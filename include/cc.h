@@ -432,12 +432,21 @@ void cc_server_destroy(cc_server* s);
  *               e.g. the array given by cc_cluster_ids_dev
  *   labels_dev  int32[n] device, written: ids renumbered 0..b-1 in order of
  *               first appearance by index
+ *
+ * The numbering runs over the n entries as one array.  For a single-job
+ * context that is exactly cc_consensus_labels.  For a batch context,
+ * cc_cluster_ids_dev holds union ids, and the result numbers the clusters
+ * of all jobs together: job 0's labels, then job 1's labels plus the number
+ * of clusters of job 0, and so on (each job's own labels, as cc_job_labels
+ * gives them, are the result's slice for that job minus its first value).
  *   stream      cudaStream_t to run on (NULL: the legacy default stream); the
  *               call synchronises it before returning
  *
  * The first call on each device looks up the device address of the fixed
  * array (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the array, so calls
+ * before any stream capture.  The address is kept for the life of the
+ * process: after a cudaDeviceReset of that device, do not call this entry
+ * point again.  All calls on a device share the array, so calls
  * that overlap on the GPU (other streams, other host threads) race and give
  * wrong labels: serialise them.  Each call resets the part it needs, so
  * nothing carries over from the previous call.  Errors are reported through
@@ -445,6 +454,9 @@ void cc_server_destroy(cc_server* s);
 #define CC_NOALLOC_MAX_N (1 << 21)
 #define CC_NOALLOC_SCRATCH_INTS (2 * CC_NOALLOC_MAX_N + CC_NOALLOC_MAX_N / 1024 + 64)
 cc_status cc_renumber_noalloc(int32_t n, const int32_t* ids_dev, int32_t* labels_dev, void* stream);
+/* CC_NOALLOC_MAX_N as compiled into the library (for bindings that cannot
+ * read this header's macros).  Never fails. */
+int32_t cc_noalloc_max_n(void);
 
 #ifdef __cplusplus
 }

@@ -26,10 +26,7 @@ EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", 
            "cc_batch_create", "cc_job_count", "cc_job_objective", "cc_job_history", "cc_job_labels",
            "cc_metrics", "cc_partition_distances", "cc_group_partitions", "cc_estimate_bytes", "cc_plan_batches", "cc_server_default_options", "cc_server_create", "cc_server_submit",
            "cc_server_progress", "cc_server_job", "cc_server_stats", "cc_server_last_error", "cc_server_destroy",
-           "cc_renumber_noalloc")
-
-# Largest n accepted by cc_renumber_noalloc (its built-in scratch holds 2 n ints).
-CC_NOALLOC_MAX_N = 1 << 21
+           "cc_renumber_noalloc", "cc_noalloc_max_n")
 
 
 class CCError(RuntimeError):
@@ -172,10 +169,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cc_server_destroy.argtypes = [P]
     lib.cc_renumber_noalloc.restype = c.c_int
     lib.cc_renumber_noalloc.argtypes = [c.c_int32, P, P, P]
+    lib.cc_noalloc_max_n.restype = c.c_int32
+    lib.cc_noalloc_max_n.argtypes = []
     return lib
 
 
 lib = load_library()
+
+# Largest n accepted by cc_renumber_noalloc, as compiled into the library
+# (its built-in scratch holds about 2 n ints).
+CC_NOALLOC_MAX_N = int(lib.cc_noalloc_max_n())
 
 
 def _check(status: int, ctx=None):

@@ -386,6 +386,10 @@ __device__ __forceinline__ long long table_build_add(Slot* t, unsigned long long
 }
 
 // ---- setup.cu ----
+// SMs of the current device (queried once per device; 1 if the query fails).
+constexpr int kMaxDevices = 64;
+int device_sm_count();
+
 // Union assembly: per-job inputs were copied into staging buffers (offsets of
 // job j at offstage[vo_j + j ..], n_j + 1 entries; columns job-local at
 // col[eo_j ..]); these kernels validate them, build the union offsets, the

@@ -16,11 +16,13 @@ namespace {
 
 constexpr int kMetBlock = 256;
 
+// Grid for grid-stride kernels: at most 8 resident blocks per SM of the current device.
 inline int met_grid(long long work)
 {
+    const long long max_blocks = 8LL * device_sm_count();
     long long b = (work + kMetBlock - 1) / kMetBlock;
     if (b < 1) b = 1;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > max_blocks) b = max_blocks;
     return (int)b;
 }
 

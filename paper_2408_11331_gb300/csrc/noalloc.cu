@@ -24,7 +24,6 @@ namespace ccg {
 
 namespace {
 
-constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 int* g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
 
@@ -134,6 +133,11 @@ __global__ void k_na_relabel(int n, const int* __restrict__ ids, const int* __re
 }  // namespace
 
 }  // namespace ccg
+
+extern "C" int32_t cc_noalloc_max_n(void)
+{
+    return CC_NOALLOC_MAX_N;
+}
 
 extern "C" cc_status cc_renumber_noalloc(int32_t n, const int32_t* ids_dev, int32_t* labels_dev, void* stream)
 {

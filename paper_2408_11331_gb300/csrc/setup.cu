@@ -4,18 +4,37 @@
 // state, the contingency hash rebuild with its summary rows, and the
 // from-scratch objective used for checks.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 
 #include "cc_internal.cuh"
 
 namespace ccg {
 
+int device_sm_count()
+{
+    static std::atomic<int> cache[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < kMaxDevices) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    if (dev < kMaxDevices) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
 namespace {
 
 constexpr int kSetupBlock = 256;
 
-inline int grid_for(long long work, int per_block = kSetupBlock, int max_blocks = 152 * 16)
+// Grid for grid-stride kernels: one block per kSetupBlock items, at most 16
+// resident blocks per SM of the current device.
+inline int grid_for(long long work, int per_block = kSetupBlock)
 {
+    const long long max_blocks = 16LL * device_sm_count();
     long long b = (work + per_block - 1) / per_block;
     if (b < 1) b = 1;
     if (b > max_blocks) b = max_blocks;

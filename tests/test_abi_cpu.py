@@ -40,6 +40,15 @@ def test_exports_every_declared_symbol(native):
     assert set(native.EXPORTS) == declared
 
 
+def test_noalloc_limit_matches_header(native):
+    """The no-allocation renumbering's size limit, as the library reports it,
+    is the one include/cc.h states (bindings read it from the library)."""
+    text = open(os.path.join(ROOT, "include", "cc.h")).read()
+    m = re.search(r"#define\s+CC_NOALLOC_MAX_N\s+\(1\s*<<\s*(\d+)\)", text)
+    assert m, "CC_NOALLOC_MAX_N not found in cc.h"
+    assert native.lib.cc_noalloc_max_n() == 1 << int(m.group(1)) == native.CC_NOALLOC_MAX_N
+
+
 def test_default_options(native):
     o = native.cc_default_options()
     assert o.max_sweeps == 20 and o.debug_checks == 0 and o.table_log2 == 0 and o.table_start_log2 == 0

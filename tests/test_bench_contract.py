@@ -43,3 +43,46 @@ def test_reference_batch_line():
     d = _run("--workload", "batch", "--jobs", "8", "--pool", "2")
     _check_common(d)
     assert d["unit"] == "jobs/s" and d["config"]["jobs"] == 8
+
+
+def _bench_module():
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    return bench
+
+
+def test_byte_model_counts_candidates():
+    """The roofline's algorithmic bytes: distinct (vertex, other cluster)
+    pairs over the CSR and the per-candidate unit costs, checked against a
+    plain enumeration on a small graph (torch on the CPU)."""
+    import numpy as np
+    import torch
+
+    sys.path.insert(0, ROOT)
+    from workloads import make_config
+
+    bench = _bench_module()
+    c = make_config("sbm", n=300, communities=5, k=6, seed=3)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    k, n = lab.shape
+    rng = np.random.default_rng(0)
+    C = rng.integers(0, 40, n).astype(np.int32)
+    C[:40] = np.arange(40)  # every id a vertex of its cluster
+    model = bench.ByteModel(torch, ro, col, k, "cpu")
+    b, q = model(C)
+    pairs = set()
+    for v in range(n):
+        for e in range(ro[v], ro[v + 1]):
+            u = int(col[e])
+            if u != v and C[u] != C[v]:
+                pairs.add((v, int(C[u])))
+    size = np.bincount(C, minlength=n)
+    single = sum(1 for _, x in pairs if size[x] == 1)
+    own_multi = int((size[C] > 1).sum())
+    nnz = len(col)
+    want = 8 * (n + 1) + 8 * nnz + 4 * k * n + 8 * n + 4 * len(pairs) + 4 * k * single \
+        + 12 * k * (len(pairs) - single) + 12 * k * own_multi
+    assert q == len(pairs) and b == want

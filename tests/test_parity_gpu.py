@@ -402,6 +402,31 @@ def test_full_size_lfr_as_benchmarked(cc):
         np.testing.assert_array_equal(job.consensus_labels(), oracle.renumber(ref.C))
 
 
+def test_full_size_knn_as_benchmarked(cc):
+    """The largest single-GPU workload at full size (kNN-15 of a 200-component
+    Gaussian mixture in 50-D, n = 2,000,000, k = 50 graded partitions; lanes
+    per item chosen automatically: 8), launched as bench.py launches it (a
+    caller stream, reset then run to convergence, twice): every sweep record,
+    the raw ids, the labels (n above 2^20, so the renumbering scans its block
+    counts several per thread) and F equal the oracle's."""
+    import torch
+
+    c = make_config("knn", device="cuda")
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    assert lab.shape == (50, 2_000_000)
+    ref = oracle.sync_run(ro, col, lab, 20)
+    stream = torch.cuda.Stream()
+    with cc.Consensus(ro, col, lab) as job:
+        job.set_stream(stream.cuda_stream)
+        for _ in range(2):
+            job.reset()
+            assert job.run_until_converged(20) == ref.sweeps
+            assert job.history() == ref.stats
+            np.testing.assert_array_equal(job.cluster_ids(), ref.C)
+        assert job.objective() == ref.F == job.objective_recompute()
+        np.testing.assert_array_equal(job.consensus_labels(), oracle.renumber(ref.C))
+
+
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("n,k,seed", [(20000, 8, 11), (5003, 37, 12), (12000, 64, 14)])
 def test_active_set_runs(cc, n, k, seed, mode):

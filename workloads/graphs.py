@@ -210,15 +210,21 @@ def knn_mixture(n: int, comps: int, dim: int, knn: int, rng, mean_scale: float =
     dev = torch.device(device)
     X = torch.from_numpy(x).to(dev)
     sq = (X * X).sum(1)
-    tile = 2048 if device == "cpu" else 8192
+    tile = 2048 if device == "cpu" else 4096
     nbr = torch.empty((n, knn), dtype=torch.int64, device=dev)
     for s in range(0, n, tile):
         e = min(n, s + tile)
-        d = sq[s:e, None] - 2.0 * (X[s:e] @ X.T) + sq[None, :]
+        # |x_r - x_u|^2 = |x_r|^2 + |x_u|^2 - 2 x_r.x_u; |x_r|^2 is the same for
+        # every u of row r, so ranking |x_u|^2 - 2 x_r.x_u (one fused matmul)
+        # gives the same neighbours
+        d = torch.addmm(sq[None, :], X[s:e], X.T, beta=1.0, alpha=-2.0)
         d[torch.arange(e - s, device=dev), torch.arange(s, e, device=dev)] = float("inf")
         nbr[s:e] = torch.topk(d, knn, dim=1, largest=False).indices
         del d
     nb = nbr.cpu().numpy()
+    del X, sq, nbr
+    if dev.type == "cuda":
+        torch.cuda.empty_cache()
     u = np.repeat(np.arange(n, dtype=np.int64), knn)
     row_off, col = csr_from_edges(n, u, nb.ravel())
     return row_off, col, truth
