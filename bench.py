@@ -20,8 +20,8 @@ Multi-GPU: a single job does not shard, so N processes run N independent
 replicas of the job (weak scaling, no collective on the data path).
 
 --impl reference times the CPU oracle (the method written out plainly in C,
-OpenMP over vertices) on the headline workload; each step is its first
-synchronous sweep from the singleton start.
+OpenMP over vertices) on the headline workload; each step is its proposal
+pass from the singleton start for one block of n/8 vertices (blocks in turn).
 
 --workload batch: the batched form.  4,096 jobs (n log-uniform in
 [200, 200000], half SBM and half LFR-style, k uniform in [5, 64]) drawn from a
@@ -235,20 +235,35 @@ def run_reference(args, rank, world):
     nnz = len(col)
     cores = os.cpu_count() or 1
     steps = args.steps or 10
-    for _ in range(args.warmup):
-        oracle.sync_step(ro, col, lab, oracle.singletons(n))
+    # one step: the oracle's proposal pass (every vertex's best move, Eq.
+    # objective4, against the singleton start) for one block of n / 8
+    # vertices, blocks taken in turn, so that a run of K + W steps stays
+    # within minutes on the host cores
+    blocks = 8
+    bounds = [n * b // blocks for b in range(blocks + 1)]
+    C0 = oracle.singletons(n)
+
+    def step(s):
+        b = s % blocks
+        oracle.sync_propose_range(ro, col, lab, C0, bounds[b], bounds[b + 1])
+        return float(ro[bounds[b + 1]] - ro[bounds[b]]) * k
+
+    for s in range(args.warmup):
+        step(s)
+    units = 0.0
     t0 = time.perf_counter()
-    for _ in range(steps):
-        oracle.sync_step(ro, col, lab, oracle.singletons(n))
+    for s in range(steps):
+        units += step(s)
     dt = time.perf_counter() - t0
-    value = nnz * k * steps / dt
+    value = units / dt
+    sample = (f"proposal pass (best graph-restricted move of every vertex against the singleton start) of one "
+              f"block of n/{blocks} vertices per step, blocks in turn; units = the block's CSR entries x k")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
            "data": "synthetic", "config": {"workload": c["name"], "description": describe(c), "n": n,
                                             "nnz": nnz, "k": k},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": "first synchronous sweep from the singleton start over the whole graph"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

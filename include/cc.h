@@ -89,6 +89,15 @@ typedef struct {
                                once) instead of behind conditional nodes; for profilers that
                                cannot see kernels inside graphs with conditional nodes.  Results
                                are identical.  0 (default): conditional regions */
+    int32_t empty_moves;    /* 1: the move-to-empty variant.  Besides the clusters of its
+                               neighbours (Eq. objective4), a vertex v may move into a new
+                               cluster of its own, which takes the id v, provided no vertex
+                               carries the id v at the start of the sweep.  Its gain is Eq.
+                               objective3 with an empty target, sum over u in a, u != v, of
+                               (k - 2 delta_uv) = 2 (A_a - k) - k (|a| - 1), and it competes
+                               with the other candidates under the same rule (least dD, ties to
+                               the smaller id).  This changes the results (a quality variant the
+                               paper does not consider).  0 (default): the paper's candidates */
 } cc_options;
 
 /* State of the contingency hash of a context. */

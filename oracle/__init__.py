@@ -75,6 +75,9 @@ def _load():
     lib.orc_sync_propose.restype = c.c_int64
     lib.orc_sync_propose.argtypes = [c.c_int32, i64p, i32p, c.c_int32, i32p, i32p, i32p, i64p,
                                      c.c_int32, c.c_int32]
+    lib.orc_sync_propose_range.restype = c.c_int64
+    lib.orc_sync_propose_range.argtypes = [c.c_int32, i64p, i32p, c.c_int32, i32p, i32p, c.c_int32, c.c_int32,
+                                           i32p, i64p, c.c_int32, c.c_int32]
     lib.orc_sync_step.restype = c.c_int32
     lib.orc_sync_step.argtypes = [c.c_int32, i64p, i32p, c.c_int32, i32p, i32p, c.c_int64, c.c_int32,
                                   c.POINTER(SweepStats), i32p, i64p, i32p]
@@ -157,8 +160,14 @@ def gain_closed(labels, C, v: int, b: int) -> int:
     return int(_load().orc_gain_closed(n, k, lab, np.ascontiguousarray(C, dtype=np.int32), v, b))
 
 
-def sync_propose(row_off, col, labels, C, mode: int = 0, threads: int = 0):
+# mode: 0 gains from the contingency counts, 1 by member iteration (the same
+# values); empty=True adds the move-to-empty candidate (mode bit 2)
+EMPTY = 2
+
+
+def sync_propose(row_off, col, labels, C, mode: int = 0, threads: int = 0, empty: bool = False):
     """(target int32[n], gain int64[n], count): each vertex's proposal against C."""
+    mode = mode | (EMPTY if empty else 0)
     lab = _labels(labels)
     k, n = lab.shape
     target = np.empty(n, np.int32)
@@ -166,6 +175,23 @@ def sync_propose(row_off, col, labels, C, mode: int = 0, threads: int = 0):
     cnt = _load().orc_sync_propose(n, np.ascontiguousarray(row_off, dtype=np.int64),
                                    np.ascontiguousarray(col, dtype=np.int32), k, lab,
                                    np.ascontiguousarray(C, dtype=np.int32), target, gain, mode, threads)
+    if cnt < 0:
+        raise RuntimeError("oracle proposal pass failed")
+    return target, gain, int(cnt)
+
+
+def sync_propose_range(row_off, col, labels, C, v0: int, v1: int, mode: int = 0, threads: int = 0,
+                       empty: bool = False):
+    """As sync_propose, for the vertices in [v0, v1) only (the rest propose nothing)."""
+    mode = mode | (EMPTY if empty else 0)
+    lab = _labels(labels)
+    k, n = lab.shape
+    target = np.empty(n, np.int32)
+    gain = np.empty(n, np.int64)
+    cnt = _load().orc_sync_propose_range(n, np.ascontiguousarray(row_off, dtype=np.int64),
+                                         np.ascontiguousarray(col, dtype=np.int32), k, lab,
+                                         np.ascontiguousarray(C, dtype=np.int32), v0, v1, target, gain, mode,
+                                         threads)
     if cnt < 0:
         raise RuntimeError("oracle proposal pass failed")
     return target, gain, int(cnt)
@@ -180,8 +206,9 @@ class StepResult:
     moved: np.ndarray
 
 
-def sync_step(row_off, col, labels, C, F=None, mode: int = 0) -> StepResult:
+def sync_step(row_off, col, labels, C, F=None, mode: int = 0, empty: bool = False) -> StepResult:
     """One synchronous sweep from state C (not modified); returns the new state."""
+    mode = mode | (EMPTY if empty else 0)
     lab = _labels(labels)
     k, n = lab.shape
     C1 = np.array(C, dtype=np.int32, copy=True)
@@ -210,8 +237,10 @@ class RunResult:
         return self.stats[-1]["F"] if self.stats else self.F0
 
 
-def sync_run(row_off, col, labels, max_sweeps: int = 20, C0=None, mode: int = 0, threads: int = 0):
+def sync_run(row_off, col, labels, max_sweeps: int = 20, C0=None, mode: int = 0, threads: int = 0,
+             empty: bool = False):
     """Synchronous sweeps from C0 (default: singletons) until no proposal or max_sweeps."""
+    mode = mode | (EMPTY if empty else 0)
     lab = _labels(labels)
     k, n = lab.shape
     C = singletons(n) if C0 is None else np.array(C0, dtype=np.int32, copy=True)

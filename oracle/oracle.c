@@ -39,6 +39,15 @@
  *      and a proposal is committed iff it holds the least key at both its
  *      clusters;
  *   5. a sweep with no proposal ends the run, as does the sweep limit.
+ * Move-to-empty variant (mode bit 2; not in the paper, whose candidate set
+ * holds only clusters that contain a neighbour, Eq. objective4): v may also
+ * move into a new cluster of its own, which takes the id v, provided no
+ * vertex carries the id v at the sweep start (an id in use stays with its
+ * cluster).  Its gain is Eq. objective3 with an empty target,
+ *   dD(v: a -> {}) = sum_{u in a, u != v} (k - 2 delta_uv) = 2 (A_a - k) - k (|a| - 1),
+ * and it competes with the neighbour candidates under the same (dD, id) rule;
+ * the guards treat it like any other move (the singleton guard never applies:
+ * the target is empty).
  * Sequential greedy (the one-move-at-a-time alternative the paper contrasts):
  * vertices in increasing index, each move evaluated on the current state and
  * applied at once if dD < 0, same candidate set and tie rule.
@@ -232,12 +241,18 @@ int64_t orc_gain_closed(int32_t n, int32_t k, const int32_t* labels, const int32
 
 /* --------------------------------------------------- synchronous proposals */
 
-/* gain of v -> x from the contingency table (mode 0) or by member iteration
- * over the cluster lists (mode 1) */
+/* mode bits: 1 = gains by member iteration (else from the contingency
+ * table); 2 = the move-to-empty candidate */
+#define ORC_MODE_MEMBER 1
+#define ORC_MODE_EMPTY 2
+
+/* gain of v -> x from the contingency table or by member iteration over the
+ * cluster lists (x = -1: a new empty cluster) */
 static int64_t sweep_gain(const contingency* t, int32_t n, int32_t k, const int32_t* labels,
                           int32_t v, int32_t a, int64_t Aa, int32_t x, int mode)
 {
-    if (mode == 0) {
+    if (!(mode & ORC_MODE_MEMBER)) {
+        if (x < 0) return 2 * (Aa - k) - (int64_t)k * ((int64_t)t->size[a] - 1);
         int64_t Ax = ct_agree(t, labels, x, v);
         return 2 * (Aa - k - Ax) - (int64_t)k * ((int64_t)t->size[a] - 1 - t->size[x]);
     }
@@ -246,6 +261,7 @@ static int64_t sweep_gain(const contingency* t, int32_t n, int32_t k, const int3
         int32_t u = t->members[p];
         if (u != v) d += (int64_t)k - 2 * delta_uv(n, k, labels, u, v);
     }
+    if (x < 0) return d;
     for (int64_t p = t->start[x]; p < t->start[x] + t->size[x]; ++p)
         d -= (int64_t)k - 2 * delta_uv(n, k, labels, t->members[p], v);
     return d;
@@ -253,9 +269,22 @@ static int64_t sweep_gain(const contingency* t, int32_t n, int32_t k, const int3
 
 /* Best move of every vertex against state C (Eq. objective4).  target[v] = -1
  * when v does not propose.  Returns the number of proposals, -1 on error. */
+static int64_t sync_propose_range(const contingency* t, int32_t n, const int64_t* row_off, const int32_t* col,
+                                  int32_t k, const int32_t* labels, const int32_t* C,
+                                  int32_t* target, int64_t* gain, int mode, int32_t v0, int32_t v1);
+
 static int64_t sync_propose(const contingency* t, int32_t n, const int64_t* row_off, const int32_t* col,
                             int32_t k, const int32_t* labels, const int32_t* C,
                             int32_t* target, int64_t* gain, int mode)
+{
+    return sync_propose_range(t, n, row_off, col, k, labels, C, target, gain, mode, 0, n);
+}
+
+/* The proposals of the vertices v0 <= v < v1 only (the others get no
+ * proposal); used to time a bounded block of the work. */
+static int64_t sync_propose_range(const contingency* t, int32_t n, const int64_t* row_off, const int32_t* col,
+                                  int32_t k, const int32_t* labels, const int32_t* C,
+                                  int32_t* target, int64_t* gain, int mode, int32_t v0, int32_t v1)
 {
     int32_t maxdeg = 0;
     for (int32_t v = 0; v < n; ++v) {
@@ -275,7 +304,7 @@ static int64_t sync_propose(const contingency* t, int32_t n, const int64_t* row_
         for (int32_t v = 0; v < n; ++v) {
             target[v] = -1;
             gain[v] = 0;
-            if (!cand) continue;
+            if (!cand || v < v0 || v >= v1) continue;
             int32_t a = C[v];
             int64_t m = 0;
             for (int64_t e = row_off[v]; e < row_off[v + 1]; ++e) {
@@ -283,15 +312,21 @@ static int64_t sync_propose(const contingency* t, int32_t n, const int64_t* row_
                 if (u == v || C[u] == a) continue;
                 cand[m++] = C[u];
             }
-            if (m == 0) continue;
+            /* the empty cluster with id v, if that id is free */
+            const int empty = (mode & ORC_MODE_EMPTY) && t->size[v] == 0;
+            if (m == 0 && !empty) continue;
             qsort(cand, (size_t)m, sizeof(int32_t), cmp_i32);
-            int64_t Aa = mode == 0 ? ct_agree(t, labels, a, v) : 0;
+            int64_t Aa = (mode & ORC_MODE_MEMBER) ? 0 : ct_agree(t, labels, a, v);
             int64_t best = 0;
             int32_t best_x = -1;
             for (int64_t j = 0; j < m; ++j) {
                 if (j > 0 && cand[j] == cand[j - 1]) continue;
                 int64_t g = sweep_gain(t, n, k, labels, v, a, Aa, cand[j], mode);
                 if (best_x < 0 || g < best) { best = g; best_x = cand[j]; }  /* ascending ids: ties keep the smaller */
+            }
+            if (empty) {
+                int64_t g = sweep_gain(t, n, k, labels, v, a, Aa, -1, mode);
+                if (best_x < 0 || g < best || (g == best && v < best_x)) { best = g; best_x = v; }
             }
             if (best < 0) { target[v] = best_x; gain[v] = best; ++count; }
         }
@@ -349,6 +384,22 @@ int64_t orc_sync_propose(int32_t n, const int64_t* row_off, const int32_t* col, 
     contingency t;
     if (ct_build(&t, n, k, labels, C) != ORC_OK) return -1;
     int64_t r = sync_propose(&t, n, row_off, col, k, labels, C, target, gain, mode);
+    ct_free(&t);
+    return r;
+}
+
+/* Proposals of the vertices in [v0, v1) against state C (the others: none). */
+int64_t orc_sync_propose_range(int32_t n, const int64_t* row_off, const int32_t* col, int32_t k,
+                               const int32_t* labels, const int32_t* C, int32_t v0, int32_t v1,
+                               int32_t* target, int64_t* gain, int32_t mode, int32_t threads)
+{
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    (void)threads;
+    contingency t;
+    if (ct_build(&t, n, k, labels, C) != ORC_OK) return -1;
+    int64_t r = sync_propose_range(&t, n, row_off, col, k, labels, C, target, gain, mode, v0, v1);
     ct_free(&t);
     return r;
 }

@@ -39,7 +39,7 @@ class cc_options(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("table_log2", ctypes.c_int32), ("table_start_log2", ctypes.c_int32),
                 ("sweep_mode", ctypes.c_int32), ("lanes", ctypes.c_int32), ("active_set", ctypes.c_int32),
-                ("no_regions", ctypes.c_int32)]
+                ("no_regions", ctypes.c_int32), ("empty_moves", ctypes.c_int32)]
 
 
 class cc_table_info(ctypes.Structure):

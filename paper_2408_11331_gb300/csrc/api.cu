@@ -357,6 +357,7 @@ cc_status check_options(const cc_options& opt, std::string* msg)
     if (opt.lanes < 0 || opt.lanes > 32 || (opt.lanes & (opt.lanes - 1)) != 0)
         return bad(CC_ERR_INVALID, "lanes must be 0 or a power of two up to 32");
     if (opt.active_set != 0 && opt.active_set != 1) return bad(CC_ERR_INVALID, "active_set must be 0 or 1");
+    if (opt.empty_moves != 0 && opt.empty_moves != 1) return bad(CC_ERR_INVALID, "empty_moves must be 0 or 1");
     return CC_OK;
 }
 
@@ -645,6 +646,7 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     a.sweep_mode = c->opt.sweep_mode;
     a.gs = c->opt.lanes > 0 ? c->opt.lanes : lanes_for_k(kmax);
     a.active_set = c->opt.active_set;
+    a.empty_moves = c->opt.empty_moves;
     a.chg = c->chg;
     a.prev = c->prev;
     a.act = c->act;

@@ -131,6 +131,7 @@ struct SweepArgs {
     int sweep_mode;              // 0 automatic, 1 always staged deltas, 2 always rebuild
     int gs;                      // lanes that score one item (a power of two, 1..32)
     int active_set;              // 1: score only the active vertices (cc_options.active_set)
+    int empty_moves;             // 1: a vertex may also move into a new cluster with its own id (cc_options.empty_moves)
     int* chg;                   // per cluster id: stamp of the last sweep that moved a vertex into or out of it
     unsigned long long* prev;   // per vertex: its bid of the last sweep that scored it (kEmpty: none)
     unsigned char* act;         // per vertex: 1 if all its candidates are scored in this sweep

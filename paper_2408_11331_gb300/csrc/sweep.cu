@@ -308,7 +308,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
             const bool full = own || (p != kEmpty && a.chg[(int)(unsigned)(p & 0xffffffffull)] == last);
             a.act[v] = full ? 1 : 0;
         }
-        if (!__any_sync(kFull, on)) continue;  // no vertex to score in this group of the warp
+        // move-to-empty variant: the empty cluster with id v is a candidate
+        // while no vertex carries that id (sizes are those of the sweep start)
+        const bool iso = a.empty_moves && run && __ldg(a.size + v) == 0;
+        if (!__any_sync(kFull, on || iso)) continue;  // nothing to score in this group of the warp
         const JobInfo J = kSingle ? J0 : a.job[j];
         const int sa = on ? __ldg(a.size + cv) : 1;
         const int* gv = a.G + row_of(J, on ? v : J.vo);
@@ -318,7 +321,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
             pb = probe_part(a, J, a.table, mask, gv, cv, sa, l, gs);
         }
         const int A = group_sum(ex + pb, gs);
-        if (on && l == 0) a.aown[v] = sa > 1 ? A : J.k;
+        const int Aa = sa > 1 ? A : J.k;
+        if (on && l == 0) a.aown[v] = Aa;
+        if (iso && l == 0) {
+            // Eq. objective3 with an empty target: 2 (A_a - k) - k (|a| - 1);
+            // A_a is kept in aown[] when v's cluster did not change
+            const int s_own = __ldg(a.size + cv);
+            const int A_own = on ? Aa : a.aown[v];
+            const int dD = 2 * (A_own - J.k) - J.k * (s_own - 1);
+            if (dD < 0) atomicMin(&a.best[v], pack_key(dD, (int)v));
+        }
     }
 }
 

@@ -243,3 +243,29 @@ def test_batch_active_set(cc, mode):
     with cc.ConsensusBatch(jobs, options(cc, sweep_mode=mode, active_set=1)) as b:
         assert b.run_until_converged(20) == max(r.sweeps for r in refs)
         _check_batch(b, jobs, refs)
+
+
+def test_batch_empty_moves(cc):
+    """The move-to-empty variant in a batch from job-local warm starts: each
+    job equals the oracle's variant started from the same consensus."""
+    jobs = _mixed_jobs(4, 515)
+    rng = np.random.default_rng(10)
+    C0 = []
+    for ro, _, lab in jobs:
+        n = len(ro) - 1
+        cls = rng.integers(0, max(1, n // 30), n)
+        C = np.empty(n, np.int32)
+        for g in np.unique(cls):
+            mem = np.nonzero(cls == g)[0]
+            C[mem] = rng.choice(mem)
+        C0.append(C)
+    o = cc.cc_default_options()
+    o.empty_moves = 1
+    with cc.ConsensusBatch(jobs, o) as b:
+        b.set_cluster_ids(np.concatenate(C0))
+        b.run_until_converged(30)
+        ids = b.cluster_ids()
+        for j, (ro, col, lab) in enumerate(jobs):
+            r = oracle.sync_run(ro, col, lab, 30, C0=C0[j], empty=True)
+            assert b.history(j) == r.stats
+            np.testing.assert_array_equal(ids[b.offsets[j]:b.offsets[j + 1]], r.C)

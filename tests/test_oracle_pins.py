@@ -509,3 +509,129 @@ def test_gain_modes_same_trajectory():
     b = oracle.sync_run(c["row_off"], c["col"], c["labels"], 20, mode=1)
     np.testing.assert_array_equal(a.C, b.C)
     assert a.stats == b.stats
+
+
+# ------------------------------------------- move-to-empty variant (option)
+
+
+def _brute_proposals_empty(row_off, col, labels, C):
+    """Best move of each vertex with the empty cluster of id v among the
+    candidates when no vertex carries that id; every gain from the pinned
+    objective: dD = (F(after) - F(before)) / 2."""
+    n = len(C)
+    F = oracle.objective(labels, C)
+    size = np.bincount(C, minlength=n)
+    target = np.full(n, -1, np.int32)
+    gain = np.zeros(n, np.int64)
+    for v in range(n):
+        cands = {int(C[u]) for u in col[row_off[v]:row_off[v + 1]] if u != v} - {int(C[v])}
+        if size[v] == 0:
+            cands.add(v)
+        best = None
+        for x in sorted(cands):
+            C2 = C.copy()
+            C2[v] = x
+            d2 = oracle.objective(labels, C2) - F
+            assert d2 % 2 == 0
+            if best is None or d2 // 2 < best[0]:
+                best = (d2 // 2, x)
+        if best is not None and best[0] < 0:
+            gain[v], target[v] = best
+    return target, gain
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("mode", [0, 1])
+def test_empty_move_proposals_are_brute_force_argmin(seed, mode):
+    """Move-to-empty variant: every proposal is the argmin over the neighbours'
+    clusters and, when the id v is free, the empty cluster v (ties to the
+    smaller id), each gain recomputed from the objective; both gain forms."""
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(5, 40))
+    k = int(rng.integers(1, 6))
+    labels, C = _random_case(rng, n, k, int(rng.integers(1, 4)), int(rng.integers(1, max(2, n // 3))))
+    row_off, col = _random_graph(rng, n, 0.2)
+    t, g, cnt = oracle.sync_propose(row_off, col, labels, C, mode=mode, empty=True)
+    bt, bg = _brute_proposals_empty(row_off, col, labels, C)
+    np.testing.assert_array_equal(t, bt)
+    np.testing.assert_array_equal(g, bg)
+    assert cnt == int((bt >= 0).sum())
+    assert np.any(bt == np.arange(n)) or seed > 3  # the empty move is exercised
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_empty_move_gain_closed_form(seed):
+    """The empty-target gain 2 (A_a - k) - k (|a| - 1) (closed form, a free
+    id b) equals the member form and half the objective difference."""
+    rng = np.random.default_rng(800 + seed)
+    n = int(rng.integers(3, 30))
+    k = int(rng.integers(1, 6))
+    labels, C = _random_case(rng, n, k, int(rng.integers(1, 5)), int(rng.integers(1, max(2, n // 2))))
+    F = oracle.objective(labels, C)
+    size = np.bincount(C, minlength=n)
+    for v in range(n):
+        if size[v] != 0:
+            continue
+        gm = oracle.gain_member(labels, C, v, v)
+        gc = oracle.gain_closed(labels, C, v, v)
+        C2 = C.copy()
+        C2[v] = v
+        assert gm == gc and oracle.objective(labels, C2) - F == 2 * gm
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_empty_move_sweeps_follow_rule(seed):
+    """With the variant, each sweep is the written rule (guards, matching)
+    applied to the brute-force proposals, F falls strictly on every sweep that
+    moves, and no vertex ever carries an id that another cluster holds."""
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(8, 36))
+    k = int(rng.integers(2, 6))
+    labels, C = _random_case(rng, n, k, int(rng.integers(2, 4)), int(rng.integers(1, 4)))
+    row_off, col = _random_graph(rng, n, 0.2)
+    F = oracle.objective(labels, C)
+    for _ in range(8):
+        bt, bg = _brute_proposals_empty(row_off, col, labels, C)
+        want_C, want = _apply_rule(C, bt, bg, labels, F)
+        r = oracle.sync_step(row_off, col, labels, C, F, empty=True)
+        assert r.stats == want
+        np.testing.assert_array_equal(r.C, want_C)
+        if r.stats["moves"]:
+            assert r.stats["F"] < F
+        C, F = r.C, r.stats["F"]
+        if r.stats["proposals"] == 0:
+            break
+
+
+def test_golden_empty_move():
+    g = _golden("empty_move_path3.json")
+    e = np.array(g["edges"])
+    row_off, col = csr_from_edges(g["n"], e[:, 0], e[:, 1])
+    labels = np.array(g["labels"], np.int32)
+    C = np.array(g["C0"], np.int32)
+    assert oracle.objective(labels, C) == g["F0"]
+    # the base rule has no candidate here
+    assert oracle.sync_step(row_off, col, labels, C).stats["proposals"] == 0
+    F = g["F0"]
+    for s, want in enumerate(g["sweeps"]):
+        r = oracle.sync_step(row_off, col, labels, C, F, empty=True)
+        for key in ("proposals", "p1", "dF_p1", "fallback", "moves", "F"):
+            assert r.stats[key] == want[key], key
+        np.testing.assert_array_equal(r.C, want["C"])
+        if s == 0:
+            assert r.gain[2] == want["gain_v2"] and r.target[2] == 2
+        C, F = r.C, r.stats["F"]
+
+
+def test_propose_range_is_a_slice():
+    """The block-restricted proposal pass (used to time a bounded sample)
+    gives exactly the full pass's proposals inside the block and none outside."""
+    c = make_config("sbm", n=300, communities=5, k=4, seed=4)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    C = oracle.singletons(300)
+    t, g, cnt = oracle.sync_propose(ro, col, lab, C)
+    tr, gr, cr = oracle.sync_propose_range(ro, col, lab, C, 100, 220)
+    np.testing.assert_array_equal(tr[100:220], t[100:220])
+    np.testing.assert_array_equal(gr[100:220], g[100:220])
+    assert np.all(tr[:100] == -1) and np.all(tr[220:] == -1)
+    assert cr == int((t[100:220] >= 0).sum())

@@ -496,3 +496,67 @@ def test_no_regions_same_results(cc, mode):
         base = job.launch_count()
         done = job.run_until_converged(20)
         assert job.launch_count() - base == 1 + ((done + 3) // 4) * 4 * 43
+
+
+# --------------------------------------------- move-to-empty variant (option)
+
+
+def _random_grouping(rng, n, groups):
+    """A warm start: vertices grouped at random, each group's id a random
+    member (so most ids are free for the move-to-empty variant)."""
+    cls = rng.integers(0, groups, n)
+    C = np.empty(n, np.int32)
+    for g in np.unique(cls):
+        mem = np.nonzero(cls == g)[0]
+        C[mem] = rng.choice(mem)
+    return C
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("active", [0, 1])
+def test_empty_moves_warm_start(cc, mode, active):
+    """cc_options.empty_moves from random groupings (many vertices in the
+    wrong cluster, most ids free): sweep by sweep, the records and raw ids
+    equal the oracle's variant, in every sweep mode, with and without the
+    active set; the empty move is taken."""
+    isolated = 0
+    for seed, (n, k) in enumerate([(3000, 8), (1500, 37), (4000, 3)]):
+        c = make_config("lfr", n=n, k=k, cmin=20, cmax=300, max_deg=min(300, n // 4), seed=40 + seed)
+        ro, col, lab = c["row_off"], c["col"], c["labels"]
+        rng = np.random.default_rng(50 + seed)
+        C = _random_grouping(rng, n, n // 40)
+        ref = oracle.sync_run(ro, col, lab, 30, C0=C, empty=True)
+        with cc.Consensus(ro, col, lab, options(cc, sweep_mode=mode, active_set=active, empty_moves=1)) as job:
+            job.set_cluster_ids(C)
+            assert job.run_until_converged(30) == ref.sweeps
+            assert job.history() == ref.stats
+            np.testing.assert_array_equal(job.cluster_ids(), ref.C)
+            assert job.objective() == ref.F == job.objective_recompute()
+        sizes = np.bincount(ref.C, minlength=n)
+        isolated += int(np.sum((ref.C == np.arange(n)) & (C != np.arange(n))))
+    assert isolated > 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_empty_moves_from_singletons(cc, mode):
+    """The variant from the singleton start on the small SBM and a kNN graph:
+    equal to the oracle's variant, sweep by sweep."""
+    for c in (make_config("sbm"), make_config("knn", n=6000, comps=30, dim=20, k=12, seed=21)):
+        ro, col, lab = c["row_off"], c["col"], c["labels"]
+        ref = oracle.sync_run(ro, col, lab, 30, empty=True)
+        assert_same(gpu_run(cc, ro, col, lab, 30, sweep_mode=mode, empty_moves=1), ref)
+
+
+def test_empty_moves_golden(cc):
+    """The hand-worked sweep where a vertex leaves its cluster for a new one."""
+    with open(os.path.join(GOLDEN, "empty_move_path3.json")) as f:
+        g = json.load(f)
+    ro, col = _edges(g["n"], g["edges"])
+    lab = np.array(g["labels"], np.int32)
+    with cc.Consensus(ro, col, lab, options(cc, empty_moves=1)) as job:
+        job.set_cluster_ids(np.array(g["C0"], np.int32))
+        assert job.objective() == g["F0"]
+        for want in g["sweeps"]:
+            info = job.sweep()
+            assert info == {key: want[key] for key in info}
+            np.testing.assert_array_equal(job.cluster_ids(), want["C"])
