@@ -18,6 +18,8 @@ Functions with a pin in ``tests/test_oracle_*.py``:
 * ``sync_step`` / ``sync_run``  synchronous sweeps with the singleton and
                      exact-objective guards and the matching fallback (Parallel algorithm)
 * ``match``          the locally dominant matching used by the fallback
+* ``colour`` / ``colour_run``  colour-batched greedy: the synchronous rule applied
+                     one colour class of a greedy colouring at a time (a variant)
 * ``seq_run``        sequential greedy, one move at a time            (The algorithm)
 * ``brute_force``    exact optimum over all set partitions, n <= 12
 """
@@ -84,6 +86,13 @@ def _load():
     lib.orc_sync_run.restype = c.c_int32
     lib.orc_sync_run.argtypes = [c.c_int32, i64p, i32p, c.c_int32, i32p, i32p, c.c_int32, c.c_int32,
                                  c.c_int32, c.POINTER(SweepStats), c.POINTER(c.c_int32)]
+    lib.orc_priority.restype = c.c_uint64
+    lib.orc_priority.argtypes = [c.c_uint64]
+    lib.orc_colour.restype = c.c_int32
+    lib.orc_colour.argtypes = [c.c_int32, i64p, i32p, i32p]
+    lib.orc_colour_run.restype = c.c_int32
+    lib.orc_colour_run.argtypes = [c.c_int32, i64p, i32p, c.c_int32, i32p, i32p, i32p, c.c_int32, c.c_int32,
+                                   c.c_int32, c.c_int32, c.POINTER(SweepStats), c.POINTER(c.c_int32)]
     lib.orc_seq_run.restype = c.c_int32
     lib.orc_seq_run.argtypes = [c.c_int32, i64p, i32p, c.c_int32, i32p, i32p, c.c_int32, i64p, i64p,
                                 c.POINTER(c.c_int32)]
@@ -252,6 +261,41 @@ def sync_run(row_off, col, labels, max_sweeps: int = 20, C0=None, mode: int = 0,
                               threads, stats, ctypes.byref(done))
     if rc != 0:
         raise RuntimeError(f"oracle run failed ({rc})")
+    return RunResult(C, [stats[s].as_dict() for s in range(done.value)], done.value, F0)
+
+
+def priority(v: int) -> int:
+    """Colouring priority of vertex v: the first splitmix64 output seeded with v."""
+    return int(_load().orc_priority(v))
+
+
+def colour(row_off, col):
+    """(colour int32[n], number of colours): greedy colouring in decreasing priority."""
+    n = len(row_off) - 1
+    out = np.empty(n, np.int32)
+    cnt = _load().orc_colour(n, np.ascontiguousarray(row_off, dtype=np.int64),
+                             np.ascontiguousarray(col, dtype=np.int32), out)
+    if cnt < 0:
+        raise RuntimeError("oracle colouring failed")
+    return out, int(cnt)
+
+
+def colour_run(row_off, col, labels, max_sweeps: int = 20, C0=None, mode: int = 0, threads: int = 0,
+               empty: bool = False):
+    """Colour-batched greedy sweeps from C0 (default: singletons) until no proposal or max_sweeps."""
+    mode = mode | (EMPTY if empty else 0)
+    lab = _labels(labels)
+    k, n = lab.shape
+    C = singletons(n) if C0 is None else np.array(C0, dtype=np.int32, copy=True)
+    F0 = objective(lab, C)
+    cls, ncol = colour(row_off, col)
+    stats = (SweepStats * max(max_sweeps, 1))()
+    done = ctypes.c_int32(0)
+    rc = _load().orc_colour_run(n, np.ascontiguousarray(row_off, dtype=np.int64),
+                                np.ascontiguousarray(col, dtype=np.int32), k, lab, C, cls, ncol, max_sweeps,
+                                mode, threads, stats, ctypes.byref(done))
+    if rc != 0:
+        raise RuntimeError(f"oracle colour-batched run failed ({rc})")
     return RunResult(C, [stats[s].as_dict() for s in range(done.value)], done.value, F0)
 
 

@@ -48,6 +48,23 @@
  * and it competes with the neighbour candidates under the same (dD, id) rule;
  * the guards treat it like any other move (the singleton guard never applies:
  * the target is empty).
+ * Colour-batched greedy (a variant between the two the Parallel algorithm
+ * section contrasts -- all moves at once, one move at a time):
+ *   colouring  priority(v) = splitmix64 of v (the first output of Steele, Lea
+ *              and Flood's generator seeded with v: z = v + 0x9E3779B97F4A7C15,
+ *              z = (z ^ z >> 30) * 0xBF58476D1CE4E5B9, z = (z ^ z >> 27) *
+ *              0x94D049BB133111EB, z ^ z >> 31), a bijection, so priorities are
+ *              distinct; in decreasing priority, each vertex takes the least
+ *              colour that no neighbour coloured before it has (self-loops
+ *              ignored).  Adjacent vertices get different colours.
+ *   sweep      the colour classes c = 0, 1, ... in turn: the vertices of class c
+ *              propose against the current state (candidates, ties, dD < 0 and
+ *              the empty move if enabled as above) and the synchronous rule
+ *              (steps 3-4) applies their proposals; the next class sees the
+ *              result.  The sweep's record sums proposals, p1, dF_p1 and moves
+ *              over the classes, counts the classes that fell back, and gives F
+ *              after the last class.  A sweep with no proposal in any class ends
+ *              the run, as does the sweep limit.
  * Sequential greedy (the one-move-at-a-time alternative the paper contrasts):
  * vertices in increasing index, each move evaluated on the current state and
  * applied at once if dD < 0, same candidate set and tie rule.
@@ -271,20 +288,22 @@ static int64_t sweep_gain(const contingency* t, int32_t n, int32_t k, const int3
  * when v does not propose.  Returns the number of proposals, -1 on error. */
 static int64_t sync_propose_range(const contingency* t, int32_t n, const int64_t* row_off, const int32_t* col,
                                   int32_t k, const int32_t* labels, const int32_t* C,
-                                  int32_t* target, int64_t* gain, int mode, int32_t v0, int32_t v1);
+                                  int32_t* target, int64_t* gain, int mode, int32_t v0, int32_t v1,
+                                  const int32_t* cls, int32_t c);
 
 static int64_t sync_propose(const contingency* t, int32_t n, const int64_t* row_off, const int32_t* col,
                             int32_t k, const int32_t* labels, const int32_t* C,
                             int32_t* target, int64_t* gain, int mode)
 {
-    return sync_propose_range(t, n, row_off, col, k, labels, C, target, gain, mode, 0, n);
+    return sync_propose_range(t, n, row_off, col, k, labels, C, target, gain, mode, 0, n, NULL, 0);
 }
 
-/* The proposals of the vertices v0 <= v < v1 only (the others get no
- * proposal); used to time a bounded block of the work. */
+/* The proposals of the vertices v0 <= v < v1 only, and (cls not NULL) only
+ * of those with cls[v] == c; the others get no proposal. */
 static int64_t sync_propose_range(const contingency* t, int32_t n, const int64_t* row_off, const int32_t* col,
                                   int32_t k, const int32_t* labels, const int32_t* C,
-                                  int32_t* target, int64_t* gain, int mode, int32_t v0, int32_t v1)
+                                  int32_t* target, int64_t* gain, int mode, int32_t v0, int32_t v1,
+                                  const int32_t* cls, int32_t c)
 {
     int32_t maxdeg = 0;
     for (int32_t v = 0; v < n; ++v) {
@@ -304,7 +323,7 @@ static int64_t sync_propose_range(const contingency* t, int32_t n, const int64_t
         for (int32_t v = 0; v < n; ++v) {
             target[v] = -1;
             gain[v] = 0;
-            if (!cand || v < v0 || v >= v1) continue;
+            if (!cand || v < v0 || v >= v1 || (cls && cls[v] != c)) continue;
             int32_t a = C[v];
             int64_t m = 0;
             for (int64_t e = row_off[v]; e < row_off[v + 1]; ++e) {
@@ -399,16 +418,31 @@ int64_t orc_sync_propose_range(int32_t n, const int64_t* row_off, const int32_t*
     (void)threads;
     contingency t;
     if (ct_build(&t, n, k, labels, C) != ORC_OK) return -1;
-    int64_t r = sync_propose_range(&t, n, row_off, col, k, labels, C, target, gain, mode, v0, v1);
+    int64_t r = sync_propose_range(&t, n, row_off, col, k, labels, C, target, gain, mode, v0, v1, NULL, 0);
     ct_free(&t);
     return r;
 }
+
+static int32_t sync_step_class(int32_t n, const int64_t* row_off, const int32_t* col, int32_t k,
+                               const int32_t* labels, int32_t* C, int64_t F_in, int32_t mode,
+                               orc_sweep_stats* st, int32_t* target_out, int64_t* gain_out, int32_t* moved_out,
+                               const int32_t* cls, int32_t c);
 
 /* One synchronous sweep on C (in/out).  F_in = F(C).  Optional per-vertex
  * outputs: the proposals of this sweep (target, gain) and which vertices moved. */
 int32_t orc_sync_step(int32_t n, const int64_t* row_off, const int32_t* col, int32_t k,
                       const int32_t* labels, int32_t* C, int64_t F_in, int32_t mode,
                       orc_sweep_stats* st, int32_t* target_out, int64_t* gain_out, int32_t* moved_out)
+{
+    return sync_step_class(n, row_off, col, k, labels, C, F_in, mode, st, target_out, gain_out, moved_out, NULL, 0);
+}
+
+/* The synchronous rule applied to the proposals of the vertices with
+ * cls[v] == c (all vertices when cls is NULL). */
+static int32_t sync_step_class(int32_t n, const int64_t* row_off, const int32_t* col, int32_t k,
+                               const int32_t* labels, int32_t* C, int64_t F_in, int32_t mode,
+                               orc_sweep_stats* st, int32_t* target_out, int64_t* gain_out, int32_t* moved_out,
+                               const int32_t* cls, int32_t c)
 {
     memset(st, 0, sizeof(*st));
     contingency t;
@@ -420,7 +454,7 @@ int32_t orc_sync_step(int32_t n, const int64_t* row_off, const int32_t* col, int
     if (!target || !gain || !C1 || !moved) {
         free(target); free(gain); free(C1); free(moved); ct_free(&t); return ORC_ERR_NOMEM;
     }
-    int64_t np = sync_propose(&t, n, row_off, col, k, labels, C, target, gain, mode);
+    int64_t np = sync_propose_range(&t, n, row_off, col, k, labels, C, target, gain, mode, 0, n, cls, c);
     st->proposals = np < 0 ? 0 : np;
     st->F = F_in;
     if (np > 0) {
@@ -483,6 +517,96 @@ int32_t orc_sync_run(int32_t n, const int64_t* row_off, const int32_t* col, int3
         *sweeps_done = s + 1;
         F = stats[s].F;
         if (stats[s].proposals == 0) break;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------- colour-batched greedy */
+
+/* Priority of vertex v: the first output of splitmix64 seeded with v. */
+uint64_t orc_priority(uint64_t v)
+{
+    uint64_t z = v + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+typedef struct { uint64_t p; int32_t v; } orc_prio;
+
+static int cmp_prio_desc(const void* a, const void* b)
+{
+    uint64_t x = ((const orc_prio*)a)->p, y = ((const orc_prio*)b)->p;
+    return (x < y) - (x > y);
+}
+
+/* Greedy colouring in decreasing priority; colour[v] written; returns the
+ * number of colours, -1 on allocation failure. */
+int32_t orc_colour(int32_t n, const int64_t* row_off, const int32_t* col, int32_t* colour)
+{
+    orc_prio* order = (orc_prio*)malloc(((size_t)n + 1) * sizeof(orc_prio));
+    int32_t maxdeg = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t d = row_off[v + 1] - row_off[v];
+        if (d > maxdeg) maxdeg = (int32_t)d;
+    }
+    uint8_t* used = (uint8_t*)calloc((size_t)maxdeg + 2, 1);
+    if (!order || !used) { free(order); free(used); return -1; }
+    for (int32_t v = 0; v < n; ++v) { order[v].p = orc_priority((uint64_t)v); order[v].v = v; colour[v] = -1; }
+    qsort(order, (size_t)n, sizeof(orc_prio), cmp_prio_desc);
+    int32_t colours = 0;
+    for (int32_t r = 0; r < n; ++r) {
+        int32_t v = order[r].v;
+        for (int64_t e = row_off[v]; e < row_off[v + 1]; ++e) {
+            int32_t u = col[e], cu = u != v ? colour[u] : -1;
+            if (cu >= 0 && cu <= maxdeg) used[cu] = 1;
+        }
+        int32_t c = 0;
+        while (used[c]) ++c;
+        colour[v] = c;
+        if (c + 1 > colours) colours = c + 1;
+        for (int64_t e = row_off[v]; e < row_off[v + 1]; ++e) {
+            int32_t u = col[e], cu = u != v ? colour[u] : -1;
+            if (cu >= 0 && cu <= maxdeg) used[cu] = 0;
+        }
+    }
+    free(order); free(used);
+    return colours;
+}
+
+/* Colour-batched greedy sweeps from C (in/out) with the colouring colour[]
+ * (as orc_colour gives it; `colours` classes), until a sweep has no proposal
+ * or max_sweeps sweeps ran.  stats as orc_sync_run. */
+int32_t orc_colour_run(int32_t n, const int64_t* row_off, const int32_t* col, int32_t k,
+                       const int32_t* labels, int32_t* C, const int32_t* colour, int32_t colours,
+                       int32_t max_sweeps, int32_t mode, int32_t threads, orc_sweep_stats* stats,
+                       int32_t* sweeps_done)
+{
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#endif
+    (void)threads;
+    *sweeps_done = 0;
+    int64_t F = orc_objective(n, k, labels, C);
+    if (F < 0) return ORC_ERR_INVALID;
+    for (int32_t s = 0; s < max_sweeps; ++s) {
+        orc_sweep_stats tot;
+        memset(&tot, 0, sizeof(tot));
+        for (int32_t c = 0; c < colours; ++c) {
+            orc_sweep_stats st;
+            int32_t rc = sync_step_class(n, row_off, col, k, labels, C, F, mode, &st, NULL, NULL, NULL, colour, c);
+            if (rc != ORC_OK) return rc;
+            tot.proposals += st.proposals;
+            tot.p1 += st.p1;
+            tot.dF_p1 += st.dF_p1;
+            tot.fallback += st.fallback;
+            tot.moves += st.moves;
+            F = st.F;
+        }
+        tot.F = F;
+        stats[s] = tot;
+        *sweeps_done = s + 1;
+        if (tot.proposals == 0) break;
     }
     return ORC_OK;
 }

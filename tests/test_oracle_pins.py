@@ -635,3 +635,93 @@ def test_propose_range_is_a_slice():
     np.testing.assert_array_equal(gr[100:220], g[100:220])
     assert np.all(tr[:100] == -1) and np.all(tr[220:] == -1)
     assert cr == int((t[100:220] >= 0).sum())
+
+
+# ------------------------------------------- colour-batched greedy (variant)
+
+
+def test_priority_is_splitmix64():
+    """The colouring priority is the first output of splitmix64 seeded with
+    v: its published sequence for seed 0 is 0xe220a8397b1dcdaf,
+    0x6e789e6aa1b965f4, 0x06c45d188009454f (seeds 0, g, 2g with g its
+    increment 0x9E3779B97F4A7C15)."""
+    g = 0x9E3779B97F4A7C15
+    assert oracle.priority(0) == 0xE220A8397B1DCDAF
+    assert oracle.priority(g) == 0x6E789E6AA1B965F4
+    assert oracle.priority(2 * g) == 0x06C45D188009454F
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_colouring_is_proper_and_greedy(seed):
+    """Adjacent vertices get different colours, and each colour is the least
+    one that no higher-priority neighbour holds (greedy in priority order)."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(2, 300))
+    row_off, col = _random_graph(rng, n, float(rng.uniform(0.01, 0.3)))
+    cls, ncol = oracle.colour(row_off, col)
+    pri = [oracle.priority(v) for v in range(n)]
+    assert ncol == (int(cls.max()) + 1 if n else 0)
+    for v in range(n):
+        nb = [int(u) for u in col[row_off[v]:row_off[v + 1]] if u != v]
+        assert all(cls[u] != cls[v] for u in nb)
+        higher = {int(cls[u]) for u in nb if pri[u] > pri[v]}
+        assert cls[v] == min(set(range(len(higher) + 1)) - higher)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_colour_sweeps_follow_rule(seed):
+    """Each colour class is the written rule (singleton guard, exact guard,
+    matching) applied to the brute-force proposals of that class's vertices
+    against the state the earlier classes left; a sweep's record sums the
+    classes; F never rises; the run stops at a sweep without proposals."""
+    rng = np.random.default_rng(1100 + seed)
+    n = int(rng.integers(6, 30))
+    k = int(rng.integers(1, 5))
+    labels = rng.integers(0, int(rng.integers(2, 4)), size=(k, n)).astype(np.int32)
+    row_off, col = _random_graph(rng, n, 0.3)
+    cls, ncol = oracle.colour(row_off, col)
+    run = oracle.colour_run(row_off, col, labels, 30)
+    C = oracle.singletons(n)
+    F = oracle.objective(labels, C)
+    for rec in run.stats:
+        tot = dict(proposals=0, p1=0, dF_p1=0, fallback=0, moves=0)
+        for c in range(ncol):
+            bt, bg = _brute_proposals(row_off, col, labels, C)
+            bt = np.where(cls == c, bt, -1)
+            bg = np.where(cls == c, bg, 0)
+            C, st = _apply_rule(C, bt, bg, labels, F)
+            assert st["F"] <= F
+            F = st["F"]
+            for key in tot:
+                tot[key] += st[key]
+        assert rec == dict(tot, F=F)
+    np.testing.assert_array_equal(run.C, C)
+    assert run.stats[-1]["proposals"] == 0 or run.sweeps == 30
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_colour_run_bounds(seed):
+    """Against brute force over all set partitions (n <= 9): F(colour) >= F*,
+    and the end state has no improving graph-restricted move."""
+    rng = np.random.default_rng(1200 + seed)
+    n = int(rng.integers(4, 10))
+    k = int(rng.integers(1, 4))
+    labels = rng.integers(0, 3, size=(k, n)).astype(np.int32)
+    row_off, col = _random_graph(rng, n, 0.5)
+    Fstar, _ = oracle.brute_force(labels)
+    run = oracle.colour_run(row_off, col, labels, 50)
+    assert run.F >= Fstar
+    assert run.F == oracle.objective(labels, run.C)
+    t, _, cnt = oracle.sync_propose(row_off, col, labels, run.C)
+    assert cnt == 0
+
+
+def test_colour_run_recovers_identical_copies():
+    """k identical copies of P whose clusters are connected: the colour-batched
+    run ends at C = P with F = 0, as the other variants do."""
+    c = make_config("sbm", n=400, communities=8, p_in=0.3, p_out=0.01, k=1)
+    truth = c["truth"].astype(np.int32)
+    labels = np.stack([truth, truth + 100, truth * 7, truth])
+    run = oracle.colour_run(c["row_off"], c["col"], labels, 200)
+    assert run.F == 0
+    np.testing.assert_array_equal(oracle.renumber(run.C), oracle.renumber(truth))
