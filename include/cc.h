@@ -98,6 +98,20 @@ typedef struct {
                                with the other candidates under the same rule (least dD, ties to
                                the smaller id).  This changes the results (a quality variant the
                                paper does not consider).  0 (default): the paper's candidates */
+    int32_t colour_batched; /* 1: the colour-batched variant, between the paper's two (all moves
+                               at once, one move at a time; Parallel algorithm section).  The
+                               graph is coloured once: in decreasing priority (the first
+                               splitmix64 output seeded with the job-local vertex id) each vertex
+                               takes the least colour no earlier-coloured neighbour has, so
+                               adjacent vertices differ.  A sweep then runs the colour classes in
+                               turn: the vertices of one class propose against the current state
+                               and the synchronous rule (guards, matching) applies them, so each
+                               class sees the moves of the classes before it.  A sweep's record
+                               sums the classes (fallback: classes that fell back); the run stops
+                               after a sweep without any proposal.  Changes the results.  Needs
+                               active_set = 0 and fewer than 2^31 CSR entries per context.
+                               cc_last_run_timing then gives one entry per class run.  0
+                               (default): the synchronous sweep */
 } cc_options;
 
 /* State of the contingency hash of a context. */
@@ -280,7 +294,8 @@ cc_status cc_run_until_converged(cc_ctx* ctx, int32_t max_sweeps, int32_t* sweep
 /* Device time of each sweep of the last cc_run_until_converged / cc_sweep
  * call, from CUDA events recorded inside its graphs on the context's stream:
  * sweep_ms[s] covers sweep s (all its kernels), propose_ms[s] its proposal
- * kernels (k_own, k_edges, k_collect).  At most max entries are written to
+ * kernels (k_own, k_edges, k_collect); with colour_batched, entry s covers
+ * the s-th colour class run (a sweep is one run of every class).  At most max entries are written to
  * each non-NULL array; *count receives the number of sweeps timed.  A sweep
  * abandoned for lack of table space and retried is timed once per attempt. */
 cc_status cc_last_run_timing(cc_ctx* ctx, int32_t max, float* sweep_ms, float* propose_ms, int32_t* count);
@@ -363,8 +378,14 @@ cc_status cc_plan_batches(int32_t jobs, const cc_job_desc* descs, const cc_optio
  * 81..160, above 160) and of similar size (n within a factor 4 of the first
  * job's) join it while they fit.  Every context runs on its own stream, so
  * contexts admitted while others run overlap with them on the device;
- * streams of smaller contexts have higher CUDA priority.  A job's results
- * are those of running it alone.  Single-threaded:
+ * streams of smaller contexts have higher CUDA priority.  Between two graph
+ * launches of a context, every job of it whose run has stopped is released
+ * at once (labels, objective, sweeps), whatever its siblings still do, and
+ * a waiting job of the same lane bin that fits the released job's place (no
+ * more vertices, CSR entries, partitions or label rows than it) is loaded
+ * into that place and joins the running union from its singleton start
+ * (not with colour_batched).  A job's results are those of running it
+ * alone.  Single-threaded:
  * all calls on one server come from one thread at a time.  Device memory
  * comes from a memory pool of the server (stream-ordered allocation). */
 typedef struct cc_server cc_server;
@@ -383,6 +404,7 @@ typedef struct {
     int64_t max_in_flight;  /* most contexts in flight at once */
     int64_t in_flight, queued;
     int64_t budget_bytes, bytes_in_use, peak_bytes;
+    int64_t admitted_running; /* jobs loaded into the place of a finished job of a running context */
 } cc_server_info;
 
 /* Fills *o with the defaults above. */

@@ -39,7 +39,8 @@ class cc_options(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
                 ("table_log2", ctypes.c_int32), ("table_start_log2", ctypes.c_int32),
                 ("sweep_mode", ctypes.c_int32), ("lanes", ctypes.c_int32), ("active_set", ctypes.c_int32),
-                ("no_regions", ctypes.c_int32), ("empty_moves", ctypes.c_int32)]
+                ("no_regions", ctypes.c_int32), ("empty_moves", ctypes.c_int32),
+                ("colour_batched", ctypes.c_int32)]
 
 
 class cc_table_info(ctypes.Structure):
@@ -76,7 +77,7 @@ class cc_server_options(ctypes.Structure):
 class cc_server_info(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "admitted", "completed", "failed", "batches",
                                               "max_in_flight", "in_flight", "queued", "budget_bytes",
-                                              "bytes_in_use", "peak_bytes")]
+                                              "bytes_in_use", "peak_bytes", "admitted_running")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -163,6 +163,8 @@ cc_status start_state(cc_ctx* c)
     }
     c->started = true;
     s.stop = 1;
+    s.cls = 0;
+    s.ncls = c->ncls;
     s.new_mask = c->cap_start - 1;
     s.mask = c->cap_start - 1;
     std::vector<JobState> js(c->jobs);
@@ -236,15 +238,31 @@ cc_status ensure_graph(cc_ctx* c, int limit, RunGraph** out)
     return CC_OK;
 }
 
-// Sweeps per graph launch: a run launches the graph until the device says the
-// run has stopped, so at most kChunk - 1 skipped sweep bodies are submitted
-// after the last sweep.
+// Sweep bodies per graph launch: a run launches the graph until the device
+// says the run has stopped, so at most kChunk - 1 skipped sweep bodies are
+// submitted after the last sweep.  With colour_batched a body runs one colour
+// class, and a graph holds up to kClassChunk of them.
 constexpr int kChunk = 4;
+constexpr int kClassChunk = 16;
+
+int chunk_bodies(const cc_ctx* c, int limit)
+{
+    const long long bodies = (long long)limit * c->ncls;
+    const int most = c->opt.colour_batched ? kClassChunk : kChunk;
+    return bodies < most ? (int)bodies : most;
+}
+
+// Graph launches a run of `limit` sweeps may take: the bodies it needs plus
+// 64 launches for sweeps abandoned for lack of table space and retried.
+long long launch_budget(const cc_ctx* c, int limit, int chunk)
+{
+    return ((long long)limit * c->ncls + chunk - 1) / chunk + 64;
+}
 
 // Runs every job until it stops; *done = largest number of sweeps of a job in this run.
 cc_status run(cc_ctx* c, int limit, int* done)
 {
-    const int chunk = limit < kChunk ? limit : kChunk;
+    const int chunk = chunk_bodies(c, limit);
     RunGraph* g = nullptr;
     cc_status r = ensure_graph(c, chunk, &g);
     if (r != CC_OK) return r;
@@ -256,7 +274,8 @@ cc_status run(cc_ctx* c, int limit, int* done)
     int before = 0;
     // a sweep abandoned for lack of table space is retried in the next body,
     // so the number of launches is bounded by the limit plus the retries
-    for (int launch = 0; launch < limit + 64; ++launch) {
+    const long long budget = launch_budget(c, limit, chunk);
+    for (long long launch = 0; launch < budget; ++launch) {
         CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
         c->launches += (long long)chunk * (c->opt.no_regions ? kKernelsPerSweep : kKernelsOutsideRegions);
         r = read_state(c, &st);
@@ -337,6 +356,8 @@ cc_status plan_jobs(int jobs, const JobInput* in, const cc_options& opt, Plan* o
         p.kmax = std::max(p.kmax, (int)q.k);
     }
     if (p.n >= (1LL << 31)) return bad(CC_ERR_OVERFLOW, "more than 2^31 - 1 vertices in all jobs together");
+    if (opt.colour_batched && p.nnz >= (1LL << 31))
+        return bad(CC_ERR_OVERFLOW, "colour_batched needs fewer than 2^31 CSR entries in all jobs together");
     cc_status r = check_options(opt, msg);
     if (r != CC_OK) return r;
     finish_plan(p, opt);
@@ -358,6 +379,9 @@ cc_status check_options(const cc_options& opt, std::string* msg)
         return bad(CC_ERR_INVALID, "lanes must be 0 or a power of two up to 32");
     if (opt.active_set != 0 && opt.active_set != 1) return bad(CC_ERR_INVALID, "active_set must be 0 or 1");
     if (opt.empty_moves != 0 && opt.empty_moves != 1) return bad(CC_ERR_INVALID, "empty_moves must be 0 or 1");
+    if (opt.colour_batched != 0 && opt.colour_batched != 1)
+        return bad(CC_ERR_INVALID, "colour_batched must be 0 or 1");
+    if (opt.colour_batched && opt.active_set) return bad(CC_ERR_INVALID, "colour_batched needs active_set = 0");
     return CC_OK;
 }
 
@@ -379,12 +403,18 @@ void finish_plan(Plan& p, const cc_options& opt)
     p.lcap = next_pow2(2ull * p.keys + 64);
     const size_t N = (size_t)p.n, J = (size_t)jobs;
     const size_t per[] = {
-        sizeof(JobInfo) * J, sizeof(JobState) * J, 8 * (N + 1), 4 * (size_t)p.nnz, 4 * (size_t)p.nnz,
-        4 * N, 4 * (size_t)p.rows, 8 * (size_t)p.rows, 4 * N, 4 * N, 4 * N, 8 * N, 4 * N,
+        sizeof(JobInfo) * (J + 1), sizeof(JobState) * (J + 1), 8 * (N + 1), 4 * (size_t)p.nnz, 4 * (size_t)p.nnz,
+        4 * N, 4 * (size_t)p.rows, 16 * (size_t)p.rows, 4 * N, 4 * N, 4 * N, 8 * N, 4 * N,
         sizeof(Slot) * (size_t)p.cap_max, 4 * N, 4 * N, 4 * N, 4 * N, N, 4 * N, 4 * N, 4 * (N / 1024 + 2),
         4 * N, 8 * N, N, 4 * J, 8 * (J + 1), 8 * (size_t)p.parts, 8 * (size_t)p.parts,
         4 * (3 * N + N / 1024 + 64), sizeof(DevState), sizeof(cc_sweep_info) * J * (size_t)p.hist_cap};
     for (size_t b : per) p.persistent += rounded(b);
+    if (opt.colour_batched) {
+        // colour of each vertex, vertices and CSR entries listed by class,
+        // class offsets (at most max degree + 1 classes, bounded by N + 1)
+        const size_t cls[] = {4 * N, 4 * N, 4 * (size_t)p.nnz, 4 * (N + 2), 8 * (N + 2), 16 * (N + 2) + 8};
+        for (size_t b : cls) p.persistent += rounded(b);
+    }
     const size_t tmp[] = {8 * (N + J), 8 * (J + 1), 4 * (size_t)p.keys, 8 * (J + 1), 4 * (size_t)p.parts, 4 * J,
                           16 * (size_t)p.lcap};
     for (size_t b : tmp) p.temporary += rounded(b);
@@ -465,6 +495,15 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
         for (int i = 0; i < in[j].k; ++i) pjob.push_back(j);
     }
     c->pfirst = pfirst;
+    c->eo = eo;
+    c->slot_n.resize(jobs);
+    c->slot_nnz.resize(jobs);
+    c->slot_k.resize(jobs);
+    for (int j = 0; j < jobs; ++j) {
+        c->slot_n[j] = in[j].n;
+        c->slot_nnz[j] = in[j].nnz;
+        c->slot_k[j] = in[j].k;
+    }
     c->parts = (int)pjob.size();
     c->lbase.assign(jobs + 1, 0);
     for (int j = 0; j < jobs; ++j) c->lbase[j + 1] = c->lbase[j] + ((long long)c->job[j].k << c->job[j].lshift);
@@ -473,12 +512,12 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     const unsigned long long cap = plan.cap_max;
     c->cap_max = cap;
 
-    CC_TRY(dalloc(c, &c->d_job, (size_t)jobs));
+    CC_TRY(dalloc(c, &c->d_job, (size_t)jobs + 1));
     CC_TRY(dalloc(c, &c->d_pfirst, (size_t)jobs));
     CC_TRY(dalloc(c, &c->d_lbase, (size_t)jobs + 1));
     CC_TRY(dalloc(c, &c->part_sq, (size_t)plan.parts));
     CC_TRY(dalloc(c, &c->part_slog, (size_t)plan.parts));
-    CC_TRY(dalloc(c, &c->js, (size_t)jobs));
+    CC_TRY(dalloc(c, &c->js, (size_t)jobs + 1));
     CC_TRY(dalloc(c, &c->off, (size_t)N + 1));
     CC_TRY(dalloc(c, &c->col, (size_t)NNZ));
     CC_TRY(dalloc(c, &c->src, (size_t)NNZ));
@@ -505,16 +544,26 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     CC_TRY(dalloc(c, &c->scratch, 3 * (size_t)N + (size_t)N / 1024 + 64));
     CC_TRY(dalloc(c, &c->st, 1));
     CC_TRY(dalloc(c, &c->hist, (size_t)jobs * c->hist_cap));
-    CC_TRY(cudaMemcpyAsync(c->d_job, c->job.data(), sizeof(JobInfo) * jobs, cudaMemcpyHostToDevice, c->stream));
+    {
+        // entry `jobs` is an idle job (no vertices, k = 0, always stopped) for
+        // the vertices that a slot reloaded with a smaller job leaves unused
+        std::vector<JobInfo> jt(c->job);
+        jt.push_back(JobInfo{0, 0, 0, 0, 0, 0, 0});
+        CC_TRY(cudaMemcpyAsync(c->d_job, jt.data(), sizeof(JobInfo) * ((size_t)jobs + 1), cudaMemcpyHostToDevice,
+                               c->stream));
+    }
     CC_TRY(cudaMemcpyAsync(c->d_lbase, c->lbase.data(), sizeof(long long) * (jobs + 1), cudaMemcpyHostToDevice,
                            c->stream));
 
     DevState s0;
     std::memset(&s0, 0, sizeof(s0));
     CC_TRY(cudaMemcpyAsync(c->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, c->stream));
-    std::vector<JobState> js0(jobs);
-    std::memset(js0.data(), 0, sizeof(JobState) * jobs);
-    CC_TRY(cudaMemcpyAsync(c->js, js0.data(), sizeof(JobState) * jobs, cudaMemcpyHostToDevice, c->stream));
+    std::vector<JobState> js0((size_t)jobs + 1);
+    std::memset(js0.data(), 0, sizeof(JobState) * ((size_t)jobs + 1));
+    js0[jobs].stop = 1;
+    CC_TRY(cudaMemcpyAsync(c->js, js0.data(), sizeof(JobState) * ((size_t)jobs + 1), cudaMemcpyHostToDevice,
+                           c->stream));
+    js0.clear();
 
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     // staging: offsets of every job whole (n + 1 each), labels partition-major per job
@@ -662,6 +711,37 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     a.hist = c->hist;
     a.hist_cap = c->hist_cap;
 
+    if (c->opt.colour_batched) {
+        CC_TRY(dalloc(c, &c->colour, (size_t)N));
+        CC_TRY(dalloc(c, &c->vlist, (size_t)N));
+        CC_TRY(dalloc(c, &c->eidx, (size_t)NNZ));
+        CC_TRY(dalloc(c, &c->voff, (size_t)N + 2));
+        CC_TRY(dalloc(c, &c->eoff, (size_t)N + 2));
+        CC_TRY(dalloc(c, &c->ccnt, 2 * ((size_t)N + 2) + 1));
+        ColourArgs ca{};
+        ca.n = N;
+        ca.nnz = NNZ;
+        ca.off = c->off;
+        ca.col = c->col;
+        ca.jid = c->jid;
+        ca.job = c->d_job;
+        ca.colour = c->colour;
+        ca.vlist = c->vlist;
+        ca.voff = c->voff;
+        ca.eidx = c->eidx;
+        ca.eoff = c->eoff;
+        ca.cnt = c->ccnt;
+        ca.flag = reinterpret_cast<int*>(c->ccnt + 2 * ((size_t)N + 2));
+        int nc = 1;
+        CC_TRY(launch_colouring(ca, &nc, c->stream));
+        c->ncls = nc;
+        a.colour_mode = 1;
+        a.vlist = c->vlist;
+        a.voff = c->voff;
+        a.eidx = c->eidx;
+        a.eoff = c->eoff;
+    }
+
     int per_sm = 0;
     CC_TRY(prepare_propose(&per_sm));
     if (per_sm < 1) return bail(fail(c, CC_ERR_INVALID, "proposal kernel cannot be resident"));
@@ -764,6 +844,129 @@ __global__ void k_shift_ids(long long n, const int* __restrict__ in, const int* 
         out[v] = (int)((unsigned)in[v] + (unsigned)sign * (unsigned)job[jid[v]].vo);
 }
 
+// ---- loading a job into a finished job's place (served form) -------------
+
+// The new job's CSR: offsets start at 0, do not decrease, end at nnz;
+// columns lie in [0, n).
+__global__ void k_load_check(long long n, long long nnz, const long long* __restrict__ ro,
+                             const int* __restrict__ col, DevState* st)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long t = t0; t < n; t += stride)
+        if (ro[t + 1] < ro[t]) atomicCAS(&st->err, 0, (int)CC_ERR_INVALID);
+    for (long long e = t0; e < nnz; e += stride)
+        if (col[e] < 0 || col[e] >= n) atomicCAS(&st->err, 0, (int)CC_ERR_INVALID);
+    if (t0 == 0 && (ro[0] != 0 || ro[n] != nnz)) atomicCAS(&st->err, 0, (int)CC_ERR_INVALID);
+}
+
+// Place of ncap vertices from vo and nnzcap CSR entries from eo: vertex t < n
+// gets row ro[t] .. ro[t + 1], the last one also the unused entries (as
+// self-loops); vertices t >= n get empty rows and the idle job.
+__global__ void k_load_csr(long long vo, long long n, long long ncap, long long eo, long long nnz, long long nnzcap,
+                           const long long* __restrict__ ro, const int* __restrict__ col_in, int job, int idle,
+                           long long* off, int* col, int* jid)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long t = t0; t < ncap; t += stride) {
+        off[vo + t] = eo + (t < n ? ro[t] : nnzcap);
+        jid[vo + t] = t < n ? job : idle;
+    }
+    for (long long e = t0; e < nnzcap; e += stride)
+        col[eo + e] = (int)(vo + (e < nnz ? col_in[e] : n - 1));
+}
+
+__global__ void k_load_src(long long vo, long long ncap, const long long* __restrict__ off, int* src)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ncap; t += stride)
+        for (long long e = off[vo + t]; e < off[vo + t + 1]; ++e) src[e] = (int)(vo + t);
+}
+
+// Singleton state of the place's vertices (stamped as changed in the sweep
+// just run, so that the next sweep computes their own-cluster sums), the
+// summary rows of the new job's label rows, and a pending table rebuild.
+__global__ void k_load_state(SweepArgs a, long long vo, long long ncap, long long go, long long rows)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int stamp = a.st->stamp;
+    for (long long t = t0; t < ncap; t += stride) {
+        const long long v = vo + t;
+        a.C[v] = (int)v;
+        a.size[v] = 1;
+        a.dsize[v] = 0;
+        a.best[v] = kEmpty;
+        a.chg[v] = stamp;
+        a.prev[v] = kEmpty;
+        a.act[v] = 1;
+    }
+    for (long long r = t0; r < rows; r += stride) {
+        const int g = a.G[go + r];
+        a.summ[go + r] = make_int4(g, g >= 0 ? 1 : 0, -1, 0);
+    }
+    if (t0 == 0) {
+        a.st->tvalid = 0;  // the next sweep is heavy: the table is rebuilt from C
+        a.st->stop = 0;
+    }
+}
+
+// Job-local renumbering of one job (vertices vo .. vo + n - 1): first holds,
+// at each of the job's cluster ids, the least job-local index of its members.
+__global__ void k_first_min_job(long long n, long long vo, const int* __restrict__ C, int* first)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride)
+        atomicMin(&first[C[vo + t]], (int)t);
+}
+
+__global__ void k_flags_job(long long n, long long vo, const int* __restrict__ C, const int* __restrict__ first,
+                            int* flag, int* blocksum)
+{
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int f = 0;
+    if (t < n) f = first[C[vo + t]] == t;
+    if (t < n) flag[t] = f;
+    if (f) atomicAdd(&cnt, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = cnt;
+}
+
+__global__ void k_relabel_job(long long n, long long vo, const int* __restrict__ C, const int* __restrict__ first,
+                              const int* __restrict__ rank, int* out)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride)
+        out[t] = rank[first[C[vo + t]]];
+}
+
+// Renumbered labels of job j alone into scratch + 2N + vo_j (device); the
+// scratch ranges of other jobs are not touched.
+cc_status renumber_job(cc_ctx* c, int j, int** labels)
+{
+    const long long N = c->n, vo = c->job[j].vo, n = c->job[j].n;
+    int* first = c->scratch;                 // indexed by (union) cluster id: the job's ids
+    int* rank = c->scratch + N + vo;         // job-local
+    int* lab = c->scratch + 2 * (size_t)N + vo;
+    int* blocksum = c->scratch + 3 * (size_t)N;
+    const int nb = (int)((n + 1023) / 1024);
+    const int g = std::max(1, std::min(c->sms * 8, (int)((n + 255) / 256)));
+    k_first<<<g, 256, 0, c->stream>>>(n, first + vo);
+    k_first_min_job<<<g, 256, 0, c->stream>>>(n, vo, c->C, first);
+    k_flags_job<<<nb, 1024, 0, c->stream>>>(n, vo, c->C, first, rank, blocksum);
+    k_scan_counts<<<1, 1024, 0, c->stream>>>(nb, blocksum);
+    k_rank<<<nb, 1024, 0, c->stream>>>(n, rank, blocksum);
+    k_relabel_job<<<g, 256, 0, c->stream>>>(n, vo, c->C, first, rank, lab);
+    c->launches += 6;
+    CC_CUDA(c, cudaGetLastError());
+    *labels = lab;
+    return CC_OK;
+}
+
 // Renumbered labels of every vertex into scratch + 2n (device); returns that pointer.
 cc_status renumber(cc_ctx* c, int** labels)
 {
@@ -795,13 +998,16 @@ cc_status check_job(cc_ctx* c, int32_t job)
 
 cc_status launch_chunk(cc_ctx* c)
 {
-    const int chunk = c->async_limit < kChunk ? c->async_limit : kChunk;
+    const int chunk = chunk_bodies(c, c->async_limit);
     RunGraph* g = nullptr;
     cc_status r = ensure_graph(c, chunk, &g);
     if (r != CC_OK) return r;
     CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
     c->launches += (long long)chunk * (c->opt.no_regions ? kKernelsPerSweep : kKernelsOutsideRegions);
     CC_CUDA(c, cudaMemcpyAsync(c->hstate, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    if (c->hjobs)
+        CC_CUDA(c, cudaMemcpyAsync(c->hjobs, c->js, sizeof(JobState) * (size_t)c->jobs, cudaMemcpyDeviceToHost,
+                                   c->stream));
     CC_CUDA(c, cudaEventRecord(c->chunk_done, c->stream));
     c->async_launches += 1;
     return CC_OK;
@@ -817,9 +1023,10 @@ cc_status ctx_create(int jobs, const JobInput* in, bool on_device, const cc_opti
     return create_common(jobs, in, on_device, opt, stream, pool, out, priority);
 }
 
-cc_status ctx_async_start(cc_ctx* c, int limit, DevState* pinned)
+cc_status ctx_async_start(cc_ctx* c, int limit, DevState* pinned, JobState* pinned_jobs)
 {
     c->hstate = pinned;
+    c->hjobs = pinned_jobs;
     c->async_limit = limit > 0 ? limit : c->opt.max_sweeps;
     c->async_launches = 0;
     if (!c->chunk_done) CC_CUDA(c, cudaEventCreateWithFlags(&c->chunk_done, cudaEventDisableTiming));
@@ -829,6 +1036,19 @@ cc_status ctx_async_start(cc_ctx* c, int limit, DevState* pinned)
 }
 
 int ctx_async_poll(cc_ctx* c, cc_status* st)
+{
+    const int r = ctx_async_poll_step(c, st);
+    if (r != 2) return r;
+    *st = ctx_async_continue(c);
+    return *st == CC_OK ? 0 : -1;
+}
+
+cc_status ctx_async_continue(cc_ctx* c)
+{
+    return launch_chunk(c);
+}
+
+int ctx_async_poll_step(cc_ctx* c, cc_status* st)
 {
     *st = CC_OK;
     const cudaError_t q = cudaEventQuery(c->chunk_done);
@@ -843,13 +1063,12 @@ int ctx_async_poll(cc_ctx* c, cc_status* st)
         return -1;
     }
     if (s.stop) return 1;
-    // each launch runs up to 4 sweep bodies; abandoned sweeps are retried
-    if (c->async_launches > c->async_limit + 64) {
+    // each launch runs up to chunk_bodies sweep bodies; abandoned sweeps are retried
+    if (c->async_launches > launch_budget(c, c->async_limit, chunk_bodies(c, c->async_limit))) {
         *st = fail(c, CC_ERR_TABLE_FULL, "sweep retries did not converge");
         return -1;
     }
-    *st = launch_chunk(c);
-    return *st == CC_OK ? 0 : -1;
+    return 2;
 }
 
 cc_status ctx_job_results(cc_ctx* c, std::vector<long long>& F, std::vector<int>& sweeps)
@@ -875,6 +1094,160 @@ cc_status ctx_copy_labels(cc_ctx* c, const int* dev_labels, int j, int32_t* out)
 {
     const JobInfo& J = c->job[j];
     CC_CUDA(c, cudaMemcpyAsync(out, dev_labels + J.vo, sizeof(int) * (size_t)J.n, cudaMemcpyDeviceToHost, c->stream));
+    return CC_OK;
+}
+
+bool ctx_slot_fits(const cc_ctx* c, int j, const JobInput& in)
+{
+    const long long kp_new = (in.k + 3) & ~3, kp_cap = (c->slot_k[j] + 3) & ~3;
+    return !c->opt.colour_batched && in.n >= 1 && in.n <= c->slot_n[j] && in.nnz <= c->slot_nnz[j] &&
+           in.k >= 1 && in.k <= c->slot_k[j] && (long long)in.n * kp_new <= c->slot_n[j] * kp_cap &&
+           (long long)in.n * in.k <= c->slot_n[j] * (long long)c->slot_k[j] && in.k <= c->kmax;
+}
+
+cc_status ctx_load_job(cc_ctx* c, int j, const JobInput& in)
+{
+    if (j < 0 || j >= c->jobs || !ctx_slot_fits(c, j, in) || !in.row_off || !in.labels || (in.nnz > 0 && !in.col))
+        return fail(c, CC_ERR_INVALID, "job does not fit the place it is loaded into");
+    const long long n = in.n, nnz = in.nnz, k = in.k;
+    const long long ncap = c->slot_n[j], nnzcap = c->slot_nnz[j];
+    JobInfo J = c->job[j];
+    J.n = n;
+    J.k = (int)k;
+    J.kp = (int)((k + 3) & ~3);
+    J.lshift = 0;
+    while ((1LL << J.lshift) < n) ++J.lshift;
+    const long long eo = c->eo[j], keys = n * k;
+    unsigned long long lcap = 64;
+    while (lcap < 2ull * (unsigned long long)keys + 64) lcap <<= 1;
+    // staging, from the context's pool when it has one (stream-ordered)
+    std::vector<void*> temp;
+    auto tmalloc = [&](void** p, size_t bytes) {
+        bytes = bytes > 0 ? bytes : 16;
+        cudaError_t e = c->pool ? cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream) : cudaMalloc(p, bytes);
+        if (e == cudaSuccess) temp.push_back(*p);
+        return e;
+    };
+    auto cleanup = [&]() {
+        if (c->pool) {
+            for (void* p : temp) cudaFreeAsync(p, c->stream);
+        } else {
+            cudaStreamSynchronize(c->stream);
+            for (void* p : temp) cudaFree(p);
+        }
+    };
+    long long *ro = nullptr, *lo = nullptr;
+    int *col = nullptr, *lab = nullptr, *pjob = nullptr, *pfirst = nullptr;
+    void* lmap = nullptr;
+    JobInfo* dj = nullptr;
+    DevState* tst = nullptr;
+    cudaError_t e = tmalloc((void**)&ro, sizeof(long long) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = tmalloc((void**)&col, sizeof(int) * (size_t)nnz);
+    if (e == cudaSuccess) e = tmalloc((void**)&lab, sizeof(int) * (size_t)keys);
+    if (e == cudaSuccess) e = tmalloc((void**)&lo, sizeof(long long) * 2);
+    if (e == cudaSuccess) e = tmalloc((void**)&pjob, sizeof(int) * (size_t)k);
+    if (e == cudaSuccess) e = tmalloc((void**)&pfirst, sizeof(int));
+    if (e == cudaSuccess) e = tmalloc(&lmap, 16 * (size_t)lcap);
+    if (e == cudaSuccess) e = tmalloc((void**)&dj, sizeof(JobInfo));
+    if (e == cudaSuccess) e = tmalloc((void**)&tst, sizeof(DevState));
+    const long long lo_h[2] = {0, keys};
+    const int zero = 0;
+    DevState s0;
+    std::memset(&s0, 0, sizeof(s0));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ro, in.row_off, sizeof(long long) * ((size_t)n + 1), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(col, in.col, sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lab, in.labels, sizeof(int) * (size_t)keys, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lo, lo_h, sizeof(lo_h), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pjob, 0, sizeof(int) * (size_t)k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pfirst, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dj, &J, sizeof(JobInfo), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tst, &s0, sizeof(DevState), cudaMemcpyHostToDevice, c->stream);
+    const int g = std::max(1, std::min(c->sms * 8, (int)((std::max(ncap, nnzcap) + 255) / 256)));
+    // check the new job's CSR before anything of the context changes
+    if (e == cudaSuccess) {
+        k_load_check<<<g, 256, 0, c->stream>>>(n, nnz, ro, col, tst);
+        e = cudaGetLastError();
+    }
+    DevState chk;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&chk, tst, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(c, e, "load job: staging");
+    }
+    if (chk.err) {
+        cleanup();
+        return fail(c, CC_ERR_INVALID, "malformed CSR: offsets must start at 0, end at nnz and not decrease; "
+                                       "columns must lie in [0, n)");
+    }
+    // the graph into the place: offsets, columns (union ids; unused entries
+    // become self-loops of the last vertex), job of each vertex, sources
+    k_load_csr<<<g, 256, 0, c->stream>>>(J.vo, n, ncap, eo, nnz, nnzcap, ro, col, j, c->jobs, c->off, c->col, c->jid);
+    k_load_src<<<g, 256, 0, c->stream>>>(J.vo, ncap, c->off, c->src);
+    // labels: compacted as at creation, into the place's rows
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->G + J.go, 0xff, sizeof(int) * (size_t)(n * J.kp), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->part_sq + c->pfirst[j], 0, sizeof(long long) * (size_t)k, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->part_slog + c->pfirst[j], 0, sizeof(double) * (size_t)k, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->js[j], 0, sizeof(JobState), c->stream);
+    LabelArgs la{};
+    la.jobs = 1;
+    la.total = keys;
+    la.labels = lab;
+    la.lo = lo;
+    la.pjob = pjob;
+    la.pfirst = pfirst;
+    la.job = dj;
+    la.js = c->js + j;
+    la.G = c->G;
+    la.lmap = lmap;
+    la.lmask = lcap - 1;
+    la.rows = n * J.kp;
+    la.st = tst;
+    la.part_sq = c->part_sq + c->pfirst[j];
+    la.part_slog = c->part_slog + c->pfirst[j];
+    if (e == cudaSuccess) e = launch_label_kernels(la, c->stream);
+    // singleton state of the place's vertices, their summary rows, and a
+    // table rebuild in the next sweep
+    if (e == cudaSuccess) {
+        k_load_state<<<g, 256, 0, c->stream>>>(c->args, J.vo, ncap, J.go, n * J.kp);
+        e = cudaGetLastError();
+    }
+    JobState jsr;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&jsr, &c->js[j], sizeof(JobState), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&chk, tst, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(c, e, "load job");
+    }
+    if (chk.err) {
+        cleanup();
+        return fail(c, CC_ERR_CUDA, "load job: label compaction failed");
+    }
+    const long long psq = jsr.partition_sq;
+    std::memset(&jsr, 0, sizeof(jsr));
+    jsr.partition_sq = psq;
+    jsr.F = psq - k * n;
+    e = cudaMemcpyAsync(&c->js[j], &jsr, sizeof(JobState), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_job + j, &J, sizeof(JobInfo), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // jsr and J are host locals
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(c, e, "load job: records");
+    c->job[j] = J;
+    c->psq[j] = psq;
+    c->F0[j] = psq - k * n;
+    c->async_launches = 0;  // the run's launch budget starts again
+    return CC_OK;
+}
+
+cc_status ctx_job_labels_now(cc_ctx* c, int j, int32_t* out)
+{
+    int* lab = nullptr;
+    cc_status r = renumber_job(c, j, &lab);
+    if (r != CC_OK) return r;
+    CC_CUDA(c, cudaMemcpyAsync(out, lab, sizeof(int) * (size_t)c->job[j].n, cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
     return CC_OK;
 }
 

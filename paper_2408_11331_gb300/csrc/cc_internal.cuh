@@ -17,10 +17,14 @@
 //                      g = (i << s_j) | rep, rep the job-local index of the least vertex
 //                      carrying that label in partition i and 2^s_j >= n_j, so g names
 //                      (partition, label) within the job and g < 2 k_j n_j.
-//   summ  int2[...]    same layout as G, one row per cluster id: per partition i
-//                      {d, m}: d the label id that was most frequent in the cluster at
-//                      the last table rebuild, m the exact current count of d (kept by
-//                      every commit); |cluster| - m bounds the count of any other label.
+//   summ  int4[...]    same layout as G, one row per cluster id: per partition i
+//                      {d1, m1, d2, m2}: the two label ids that were most frequent in the
+//                      cluster at the last table rebuild (d1 first; -1 where the cluster
+//                      had fewer labels) and the exact current counts of each (kept by
+//                      every commit), so |cluster| - m1 - m2 bounds the count of any
+//                      other label (and is 0 when d1 and d2 cover the cluster).  The
+//                      first 8 bytes read as one unsigned 64-bit value are m1 << 32 | d1
+//                      (likewise the last 8), the order in which the rebuild ranks labels.
 //   C     int32[N]     cluster id of each vertex
 //   size  int32[N]     cluster sizes, indexed by cluster id
 //   table Slot[cap]    the contingency counts n(c, i, l) of all jobs as one open-
@@ -70,6 +74,11 @@ struct JobState {
     long long F;               // current objective
     long long recompute;       // F' accumulator (heavy sweeps, recompute)
     long long partition_sq;    // sum_i sum_j |P_ij|^2
+    long long t_prop;          // colour_batched: the sweep's totals over its classes so far:
+    long long t_p1;            //   |P|, |P1|, dF of P1, classes that fell back, moves
+    long long t_dFp1;
+    long long t_fb;
+    long long t_moves;
     int mode;                  // 0 nothing to commit, 1 commit P1 (staged), 2 matching, 3 P1 committed (rebuilt)
     int stop;                  // 1: this job's run has stopped
     int sweeps;                // sweeps recorded since creation / reset
@@ -103,6 +112,8 @@ struct DevState {
     unsigned long long region_launches;  // kernels run inside the gated regions of sweep graphs
     int stamp;                   // number of the current sweep (since creation; retried sweeps reuse it)
     int all_active;              // 1: every vertex is scored in this sweep (first sweep of a run)
+    int cls;                     // colour_batched: the class this sweep body runs
+    int ncls;                    // colour_batched: number of classes (of the job with the most)
 };
 
 // Arguments of the kernels (passed by value).
@@ -118,7 +129,7 @@ struct SweepArgs {
     const JobInfo* job;         // J
     JobState* js;               // J
     const int* G;
-    int2* summ;
+    int4* summ;
     int* C;
     int* size;
     int* dsize;                 // staged size deltas
@@ -132,6 +143,12 @@ struct SweepArgs {
     int gs;                      // lanes that score one item (a power of two, 1..32)
     int active_set;              // 1: score only the active vertices (cc_options.active_set)
     int empty_moves;             // 1: a vertex may also move into a new cluster with its own id (cc_options.empty_moves)
+    int colour_mode;             // 1: colour-batched sweeps (cc_options.colour_batched): a sweep body
+                                 //    runs the vertices of colour class st->cls only
+    const int* vlist;            // colour_batched: vertices listed class by class (n)
+    const int* voff;             // colour_batched: first entry of each class in vlist (ncls + 1)
+    const int* eidx;             // colour_batched: CSR entries of each class's vertices, class by class (nnz)
+    const long long* eoff;       // colour_batched: first entry of each class in eidx (ncls + 1)
     int* chg;                   // per cluster id: stamp of the last sweep that moved a vertex into or out of it
     unsigned long long* prev;   // per vertex: its bid of the last sweep that scored it (kEmpty: none)
     unsigned char* act;         // per vertex: 1 if all its candidates are scored in this sweep
@@ -186,13 +203,14 @@ __device__ __forceinline__ unsigned long long ckey(int c, int g)
 }
 
 // Keeps the summary row of the slot's (cluster, partition) exact after its
-// count changed by d: only the count of the row's own label is stored.
+// count changed by d: only the counts of the row's two labels are stored.
 __device__ __forceinline__ void summ_update(const SweepArgs& a, unsigned long long key, int d)
 {
     const int x = (int)(key >> 32), g = (int)(unsigned)(key & 0xffffffffull);
     const JobInfo& J = a.job[a.jid[x]];
-    int2* S = a.summ + row_of(J, x) + (g >> J.lshift);
+    int4* S = a.summ + row_of(J, x) + (g >> J.lshift);
     if (S->x == g) atomicAdd(&S->y, d);
+    else if (S->z == g) atomicAdd(&S->w, d);
 }
 
 __device__ __forceinline__ void set_err(DevState* st, int code)
@@ -359,17 +377,27 @@ __device__ __forceinline__ ulonglong2 slot_cas(Slot* p, ulonglong2 cmp, ulonglon
     return old;
 }
 
+// 16-byte compare-and-swap of a summary entry (same instruction as slot_cas).
+__device__ __forceinline__ ulonglong2 entry_cas(int4* p, ulonglong2 cmp, ulonglong2 val)
+{
+    return slot_cas(reinterpret_cast<Slot*>(p), cmp, val);
+}
+
 // Adds cnt to key's count in a table being built from a cleared state (every
 // slot either empty with count 0, or holding a key): a new key is written
 // together with its count by one 16-byte CAS; an existing key gets an atomic
 // add.  *inserted is set when this call created the slot.  Returns -1 if the
 // table is full.
+// mark (0 or 1) goes into the new slot's staged-delta field: the rebuild
+// marks the keys whose summary entry is already final (see setup.cu) and
+// clears the mark again before any sweep stages deltas.
 __device__ __forceinline__ long long table_build_add(Slot* t, unsigned long long mask, unsigned long long key, int cnt,
-                                                     bool* inserted)
+                                                     bool* inserted, int mark = 0)
 {
     *inserted = false;
     const ulonglong2 empty = make_ulonglong2(kEmpty, 0ull);
-    const ulonglong2 mine = make_ulonglong2(key, (unsigned long long)(unsigned)cnt);
+    const ulonglong2 mine =
+        make_ulonglong2(key, ((unsigned long long)(unsigned)mark << 32) | (unsigned long long)(unsigned)cnt);
     unsigned long long h = hash_key(key) & mask;
     for (unsigned long long p = 0; p <= mask; ++p) {
         const ulonglong2 old = slot_cas(t + h, empty, mine);
@@ -432,9 +460,12 @@ struct LabelArgs {
     double* part_slog;          // per global partition: sum_l |P_il| log |P_il|
 };
 cudaError_t launch_compact_labels(const LabelArgs& a, cudaStream_t s);
+// The same without filling G with -1 first (the caller has set the rows the
+// jobs of `a` write, and only those, to -1).
+cudaError_t launch_label_kernels(const LabelArgs& a, cudaStream_t s);
 
 cudaError_t launch_init_state(const SweepArgs& a, cudaStream_t s);
-// Summary rows of the singleton start ({g_i(v), 1, 0} for cluster v, padding {-1, 0, 0}).
+// Summary rows of the singleton start ({g_i(v), 1, -1, 0} for cluster v, padding {-1, 0, -1, 0}).
 cudaError_t launch_singleton_summaries(const SweepArgs& a, long long rows, cudaStream_t s);
 // Sizes from C (ids outside their job set CC_ERR_INVALID).
 cudaError_t launch_state_from_ids(const SweepArgs& a, cudaStream_t s);
@@ -470,6 +501,27 @@ struct MetricsArgs {
 cudaError_t launch_metrics(const SweepArgs& a, const MetricsArgs& m, int parts, cudaStream_t s);
 // C of job j's n vertices := its input partition i (cluster id = least vertex of the class).
 cudaError_t launch_ids_from_partition(const SweepArgs& a, long long n, int j, int i, cudaStream_t s);
+
+// Greedy colouring of every job's graph in decreasing splitmix64 priority of
+// job-local vertex ids (Jones-Plassmann rounds), then the vertices and CSR
+// entries listed class by class; *classes receives the number of classes.
+// colour, vlist (n), eidx (nnz), voff / eoff (n + 2 entries) are allocated by
+// the caller; cnt (8 (n + 2) bytes) is scratch.
+struct ColourArgs {
+    long long n, nnz;
+    const long long* off;
+    const int* col;
+    const int* jid;
+    const JobInfo* job;
+    int* colour;
+    int* vlist;
+    int* voff;
+    int* eidx;
+    long long* eoff;
+    long long* cnt;
+    int* flag;              // one int of scratch
+};
+cudaError_t launch_colouring(const ColourArgs& a, int* classes, cudaStream_t s);
 
 // ---- api.cu ----
 // Message reported by cc_last_error(NULL) in this thread.

@@ -29,6 +29,11 @@ struct cc_ctx {
     std::vector<long long> F0;          // objective of each job at the singleton start
     std::vector<long long> psq;         // sum_ij |P_ij|^2 of each job
     std::vector<int> pfirst;            // first global partition of each job
+    std::vector<long long> eo;          // first CSR entry of each job (jobs + 1)
+    // capacity of each job's place in the union (its sizes at creation): a
+    // served context can load a smaller job into a place whose job is done
+    std::vector<long long> slot_n, slot_nnz;
+    std::vector<int> slot_k;
     std::vector<long long> lbase;       // first label id of each job in a job-concatenated id space
     long long nlabels = 0;              // sum_j k_j 2^s_j
     int parts = 0;                      // sum_j k_j
@@ -43,7 +48,7 @@ struct cc_ctx {
     int* src = nullptr;
     int* jid = nullptr;
     int* G = nullptr;
-    int2* summ = nullptr;
+    int4* summ = nullptr;
     int* C = nullptr;
     int* size = nullptr;
     int* dsize = nullptr;
@@ -62,6 +67,14 @@ struct cc_ctx {
     int* cursor = nullptr;              // rebuild scratch (n)
     int* bsum = nullptr;                // rebuild scratch (n/1024 + 2)
     int* scratch = nullptr;             // 3n + n/1024 + 64 ints: output renumbering, warm starts
+    // colour_batched: colour of each vertex, vertices and CSR entries by class
+    int* colour = nullptr;
+    int* vlist = nullptr;
+    int* voff = nullptr;
+    int* eidx = nullptr;
+    long long* eoff = nullptr;
+    long long* ccnt = nullptr;          // colouring scratch (2 (n + 2)) and a flag
+    int ncls = 1;                       // colour classes (1 without colour_batched)
     ccg::DevState* st = nullptr;
     cc_sweep_info* hist = nullptr;
     int hist_cap = 0;
@@ -80,6 +93,7 @@ struct cc_ctx {
     std::string err;
     // a run driven without blocking (ctx_async_*)
     ccg::DevState* hstate = nullptr;    // pinned host copy of st, owned by the caller
+    ccg::JobState* hjobs = nullptr;     // pinned host copy of the job records, owned by the caller (or null)
     cudaEvent_t chunk_done = nullptr;   // recorded after each graph launch and the copy of st
     int async_limit = 0;
     int async_launches = 0;
@@ -128,12 +142,39 @@ cc_status ctx_create(int jobs, const JobInput* in, bool on_device, const cc_opti
 // Starts a run of at most `limit` sweeps without waiting: queues the run and
 // its first graph launch, then a copy of the control block into `pinned` and
 // an event.
-cc_status ctx_async_start(cc_ctx* c, int limit, DevState* pinned);
+cc_status ctx_async_start(cc_ctx* c, int limit, DevState* pinned, JobState* pinned_jobs = nullptr);
 
 // Checks a run started by ctx_async_start: 0 = still running (the next graph
 // launch is queued when the previous one ended without stopping), 1 = every
 // job has stopped, -1 = failed (*st holds the status).
 int ctx_async_poll(cc_ctx* c, cc_status* st);
+// As ctx_async_poll, but when a graph launch ended without stopping the run
+// it returns 2 without queueing the next launch: the pinned job records are
+// then those after that launch (a job with stop set is done and its labels
+// are final), and ctx_async_continue queues the next launch.
+int ctx_async_poll_step(cc_ctx* c, cc_status* st);
+cc_status ctx_async_continue(cc_ctx* c);
+
+// Whether a job of these sizes fits the place of job j (see ctx_load_job).
+bool ctx_slot_fits(const cc_ctx* c, int j, const JobInput& in);
+
+// Loads a new job into the place of job j, whose run has ended and whose
+// results were taken, while the context's other jobs keep running: the CSR,
+// the compacted labels and the singleton state of the new job go into job
+// j's ranges (vertices the new job does not use go to an idle job that
+// never runs; CSR entries it does not use become self-loops of its last
+// vertex, which the method ignores), job j's record restarts at the new
+// job's singleton start, and the next sweep rebuilds the contingency table
+// from C for all jobs.  The new job's results are then those of running it
+// alone.  Host inputs are read before the call returns.  The run goes on
+// with ctx_async_continue.  Errors: CC_ERR_INVALID (malformed input; the
+// context is unchanged), CC_ERR_OOM, CC_ERR_CUDA.
+cc_status ctx_load_job(cc_ctx* c, int j, const JobInput& in);
+
+// Labels of job j alone, renumbered as by cc_job_labels, into host memory
+// (blocks until they are there).  Valid once the job has stopped, also
+// while other jobs of the context still run.
+cc_status ctx_job_labels_now(cc_ctx* c, int j, int32_t* out);
 
 // Objective and sweeps of every job (synchronises the context's stream).
 cc_status ctx_job_results(cc_ctx* c, std::vector<long long>& F, std::vector<int>& sweeps);

@@ -102,7 +102,7 @@ __global__ void k_met_clusters(SweepArgs a, MetricsArgs m, int parts)
         const JobInfo& J = a.job[j];
         atomicAdd(reinterpret_cast<unsigned long long*>(m.csq + j), (unsigned long long)(s * s));
         atomicAdd(m.cslog + j, (double)s * log((double)s));
-        const int2* S = a.summ + row_of(J, x);
+        const int4* S = a.summ + row_of(J, x);
         const int P0 = m.pfirst[j];
         for (int i = 0; i < J.k; ++i)
             atomicAdd(reinterpret_cast<unsigned long long*>(sjc + P0 + i), (unsigned long long)S[i].y);

@@ -2,11 +2,18 @@
 // GPU and batches their sweeps (continuous batching).
 //
 // Submitted jobs wait in arrival order.  Each call of cc_server_progress
-//   1. polls the contexts in flight; a context whose current graph launch has
-//      ended either gets its next launch queued or, once all of its jobs have
-//      stopped, is harvested: labels renumbered on the device and copied into
-//      each job's output buffer, objective and sweep count recorded, memory
-//      returned to the server's pool;
+//   1. polls the contexts in flight; when a context's current graph launch has
+//      ended, every job of it that has stopped is released at once (its
+//      labels renumbered on the device and copied into the job's output
+//      buffer, objective and sweep count recorded), without waiting for the
+//      other jobs of its context; then the next launch is queued, or, once
+//      all of its jobs have stopped, the context's memory goes back to the
+//      server's pool;
+//      Waiting jobs of the context's lane bin that fit the place of a
+//      released job (no more vertices, CSR entries, partitions and label
+//      rows) are loaded into it before the next launch, so they join the
+//      running union between two graph launches (iteration-level batching);
+//      a context whose jobs have all stopped is kept for such jobs too;
 //   2. admits waiting jobs while a context slot is free and the device bytes
 //      of the new context (computed exactly from the job sizes before
 //      anything is allocated) fit in what the budget has left.  The oldest
@@ -46,6 +53,8 @@ struct ServerJob {
 struct Flight {
     cc_ctx* ctx = nullptr;
     std::vector<ServerJob> jobs;
+    std::vector<char> released;  // per job: labels and record delivered
+    int bin = 0;                 // lane bin of the context's jobs
     size_t bytes = 0;  // device bytes held by the context (persistent part of its plan)
     int slot = 0;      // pinned control-block slot
 };
@@ -67,6 +76,7 @@ struct cc_server {
     int device = 0;
     cudaMemPool_t pool = nullptr;
     DevState* pinned = nullptr;  // max_active control-block slots
+    JobState* pinned_jobs = nullptr;  // max_active x max_batch_jobs job records
     std::vector<int> free_slots;
     std::deque<ServerJob> queue;
     std::vector<Flight> flights;
@@ -140,44 +150,121 @@ void release(cc_server* s, size_t idx)
     s->flights.erase(s->flights.begin() + (long)idx);
 }
 
-// Harvest of a finished context: labels of every job into its buffer, then
-// objective and sweeps (the read of the job records synchronises the stream
-// after the label copies).
+JobState* flight_jobs(cc_server* s, const Flight& f)
+{
+    return s->pinned_jobs + (size_t)f.slot * (size_t)s->sopt.max_batch_jobs;
+}
+
+// Releases job j of a context whose run has stopped it: its labels alone
+// (renumbered on the device, copied into its buffer), then its record.
+// Returns 1 if a job was released.
+int release_job(cc_server* s, Flight& f, size_t j)
+{
+    if (f.released[j]) return 0;
+    const JobState& js = flight_jobs(s, f)[j];
+    cc_status st = ctx_job_labels_now(f.ctx, (int)j, f.jobs[j].out);
+    if (st != CC_OK) s->err = cc_last_error(f.ctx);
+    finish_job(s, f.jobs[j], st, st == CC_OK ? js.F : 0, st == CC_OK ? js.sweeps : 0);
+    f.released[j] = 1;
+    return 1;
+}
+
+// Loads waiting jobs into the places of released jobs of flight f (in
+// arrival order, first fit within a bounded look-ahead); returns how many.
+int refill(cc_server* s, Flight& f)
+{
+    int loaded = 0;
+    const int bin = f.jobs.empty() ? -1 : f.bin;
+    for (size_t j = 0; j < f.jobs.size() && !s->queue.empty(); ++j) {
+        if (!f.released[j]) continue;
+        const size_t look = std::min(s->queue.size(), (size_t)64);
+        for (size_t q = 0; q < look; ++q) {
+            const ServerJob& w = s->queue[q];
+            if (w.bin != bin || !ctx_slot_fits(f.ctx, (int)j, w.in)) continue;
+            const ServerJob job = w;
+            s->queue.erase(s->queue.begin() + (long)q);
+            const cc_status st = ctx_load_job(f.ctx, (int)j, job.in);
+            if (st != CC_OK) {
+                s->err = cc_last_error(f.ctx);
+                finish_job(s, job, st, 0, 0);
+                if (st != CC_ERR_INVALID) return loaded;  // the context is no longer usable
+                break;
+            }
+            f.jobs[j] = job;
+            f.released[j] = 0;
+            ++loaded;
+            s->info.admitted += 1;
+            s->info.admitted_running += 1;
+            break;
+        }
+    }
+    return loaded;
+}
+
+// Harvest of a finished context: every job not released yet, then the
+// context's memory.
 void harvest(cc_server* s, size_t idx)
 {
     Flight& f = s->flights[idx];
-    int* lab = nullptr;
-    cc_status st = ctx_renumber(f.ctx, &lab);
-    for (size_t j = 0; st == CC_OK && j < f.jobs.size(); ++j) st = ctx_copy_labels(f.ctx, lab, (int)j, f.jobs[j].out);
-    std::vector<long long> F;
-    std::vector<int> sweeps;
-    if (st == CC_OK) st = ctx_job_results(f.ctx, F, sweeps);
-    if (st != CC_OK) s->err = cc_last_error(f.ctx);
-    for (size_t j = 0; j < f.jobs.size(); ++j)
-        finish_job(s, f.jobs[j], st, st == CC_OK ? F[j] : 0, st == CC_OK ? sweeps[j] : 0);
+    for (size_t j = 0; j < f.jobs.size(); ++j) release_job(s, f, j);
     release(s, idx);
 }
 
-// Polls every context in flight; returns how many finished.
+// Polls every context in flight; returns how many jobs finished.
 int poll_flights(cc_server* s)
 {
     int finished = 0;
     for (size_t i = 0; i < s->flights.size();) {
         cc_status st = CC_OK;
-        const int r = ctx_async_poll(s->flights[i].ctx, &st);
+        Flight& f = s->flights[i];
+        const int r = ctx_async_poll_step(f.ctx, &st);
         if (r == 0) {
             ++i;
             continue;
         }
-        if (r == 1) {
-            harvest(s, i);
-        } else {
-            Flight& f = s->flights[i];
+        if (r == 2) {
+            // a launch ended and the run goes on: release the jobs that
+            // stopped, then queue the next launch
+            const JobState* js = flight_jobs(s, f);
+            for (size_t j = 0; j < f.jobs.size(); ++j)
+                if (js[j].stop) finished += release_job(s, f, j);
+            refill(s, f);
+            st = ctx_async_continue(f.ctx);
+            if (st == CC_OK) {
+                ++i;
+                continue;
+            }
             s->err = cc_last_error(f.ctx);
-            for (const ServerJob& j : f.jobs) finish_job(s, j, st, 0, 0);
+            for (size_t j = 0; j < f.jobs.size(); ++j)
+                if (!f.released[j]) finish_job(s, f.jobs[j], st, 0, 0);
+            release(s, i);
+            continue;
+        }
+        if (r == 1) {
+            // every job has stopped: release them; if waiting jobs fit their
+            // places, the context goes on with those
+            for (size_t j = 0; j < f.jobs.size(); ++j) finished += release_job(s, f, j);
+            if (refill(s, f) > 0) {
+                st = ctx_async_continue(f.ctx);
+                if (st == CC_OK) {
+                    ++i;
+                    continue;
+                }
+                s->err = cc_last_error(f.ctx);
+                for (size_t j = 0; j < f.jobs.size(); ++j)
+                    if (!f.released[j]) finish_job(s, f.jobs[j], st, 0, 0);
+            }
+            release(s, i);
+            continue;
+        } else {
+            s->err = cc_last_error(f.ctx);
+            for (size_t j = 0; j < f.jobs.size(); ++j)
+                if (!f.released[j]) {
+                    finish_job(s, f.jobs[j], st, 0, 0);
+                    ++finished;
+                }
             release(s, i);
         }
-        ++finished;
     }
     return finished;
 }
@@ -224,6 +311,8 @@ int admit(cc_server* s)
         Flight f;
         f.jobs.reserve(take.size());
         for (size_t q : take) f.jobs.push_back(s->queue[q]);
+        f.released.assign(f.jobs.size(), 0);
+        f.bin = first.bin;
         for (size_t r = take.size(); r-- > 0;) s->queue.erase(s->queue.begin() + (long)take[r]);
         std::vector<JobInput> in;
         in.reserve(f.jobs.size());
@@ -234,7 +323,9 @@ int admit(cc_server* s)
         f.slot = s->free_slots.back();
         cc_status st = ctx_create((int)in.size(), in.data(), false, &s->opt, nullptr, s->pool, &f.ctx,
                                   priority_for(s, (double)acc.keys + (double)acc.nnz));
-        if (st == CC_OK) st = ctx_async_start(f.ctx, s->opt.max_sweeps, s->pinned + f.slot);
+        if (st == CC_OK)
+            st = ctx_async_start(f.ctx, s->opt.max_sweeps, s->pinned + f.slot,
+                                 s->pinned_jobs + (size_t)f.slot * (size_t)s->sopt.max_batch_jobs);
         if (st != CC_OK) {
             s->err = f.ctx ? cc_last_error(f.ctx) : cc_last_error(nullptr);
             if (f.ctx) ctx_destroy(f.ctx);
@@ -338,6 +429,7 @@ cc_status cc_server_create(const cc_server_options* sopt, const cc_options* opt,
     auto bail = [&](cudaError_t e, const char* what) {
         g_server_error = std::string(what) + ": " + cudaGetErrorString(e);
         if (s->pinned) cudaFreeHost(s->pinned);
+        if (s->pinned_jobs) cudaFreeHost(s->pinned_jobs);
         if (s->pool) cudaMemPoolDestroy(s->pool);
         delete s;
         return e == cudaErrorMemoryAllocation ? CC_ERR_OOM : CC_ERR_CUDA;
@@ -366,6 +458,9 @@ cc_status cc_server_create(const cc_server_options* sopt, const cc_options* opt,
     if (e != cudaSuccess) return bail(e, "cudaMemPoolSetAttribute");
     e = cudaHostAlloc(reinterpret_cast<void**>(&s->pinned), sizeof(DevState) * (size_t)so.max_active,
                       cudaHostAllocDefault);
+    if (e != cudaSuccess) return bail(e, "cudaHostAlloc");
+    e = cudaHostAlloc(reinterpret_cast<void**>(&s->pinned_jobs),
+                      sizeof(JobState) * (size_t)so.max_active * (size_t)so.max_batch_jobs, cudaHostAllocDefault);
     if (e != cudaSuccess) return bail(e, "cudaHostAlloc");
     for (int i = so.max_active - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->info.budget_bytes = so.budget_bytes;
@@ -452,6 +547,7 @@ void cc_server_destroy(cc_server* s)
     s->flights.clear();
     cudaDeviceSynchronize();
     if (s->pinned) cudaFreeHost(s->pinned);
+    if (s->pinned_jobs) cudaFreeHost(s->pinned_jobs);
     if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
 }

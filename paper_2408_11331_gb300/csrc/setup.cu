@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <vector>
 
 #include "cc_internal.cuh"
 
@@ -236,7 +237,7 @@ __global__ void k_summ_singletons(SweepArgs a, long long rows)
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
         const int g = a.G[r];
-        a.summ[r] = g >= 0 ? make_int2(g, 1) : make_int2(-1, 0);
+        a.summ[r] = make_int4(g, g >= 0 ? 1 : 0, -1, 0);
     }
 }
 
@@ -289,7 +290,7 @@ __global__ void k_table_clear(SweepArgs a, long long rows, int conditional)
     const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (unsigned long long s = t0; s < cap; s += stride)
         reinterpret_cast<ulonglong2*>(a.table)[s] = make_ulonglong2(kEmpty, 0ull);
-    for (unsigned long long r = t0; r < (unsigned long long)rows; r += stride) a.summ[r] = make_int2(0, 0);
+    for (unsigned long long r = t0; r < (unsigned long long)rows; r += stride) a.summ[r] = make_int4(-1, 0, -1, 0);
     if (st->abort)
         for (unsigned long long v = t0; v < (unsigned long long)a.n; v += stride) a.dsize[v] = 0;
     if (t0 == 0) st->used = 0;
@@ -374,12 +375,35 @@ __global__ void k_members_scatter(SweepArgs a, int conditional)
     }
 }
 
-__global__ void k_table_build(SweepArgs a, int conditional)
+// Largest 64-bit value over the lanes of a contiguous lane segment [lane,
+// end) of the warp, left in the segment's first lane (every lane must call it).
+__device__ __forceinline__ unsigned long long segment_max(unsigned long long x, int lane, int end)
 {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_down_sync(0xffffffffu, x, o);
+        if (lane + o < end && y > x) x = y;
+    }
+    return x;
+}
+
+// Inserts every member's keys (partitions innermost, equal keys of a warp
+// merged with __match_any_sync and added once).  Members are listed cluster
+// by cluster, so a cluster whose members all lie in one warp's 32 entries
+// gets its exact counts inside that warp: the warp then writes the cluster's
+// summary entries itself (the two most frequent labels, ties to the larger
+// id, as the table scan would rank them), adds its keys' -2 n^2 to the job's
+// F' in a heavy sweep (eval), and marks those keys so that the scan skips
+// them.  Keys of clusters spread over several warps are left to the scan.
+__global__ void k_table_build(SweepArgs a, int conditional, int eval)
+{
+    extern __shared__ long long dyn_jobs[];
     DevState* st = a.st;
     if (rebuild_off(st, conditional)) return;
     __shared__ unsigned long long s_used;
     if (threadIdx.x == 0) s_used = 0;
+    const bool ev = eval && st->heavy;
+    JobAcc acc(ev ? job_smem_init(a.jobs, dyn_jobs) : nullptr, &a.js[0].recompute, kJobStride);
     __syncthreads();
     const unsigned long long mask = st->new_mask;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -387,39 +411,70 @@ __global__ void k_table_build(SweepArgs a, int conditional)
     unsigned long long used = 0;  // slots this warp created (lane 0 counts)
     for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += stride) {
         const long long m = base + threadIdx.x;
+        const long long wb = m - lane;  // first member of this warp's window
         const bool valid = m < a.n;
-        int v = 0, c = 0, k = 0;
+        int v = 0, c = 0, k = 0, job = 0, seg_end = lane + 1;
+        bool whole = false;
         const int* row = a.G;
+        int4* S = a.summ;
         if (valid) {
             v = a.members[m];
             c = a.C[v];
-            const JobInfo& J = a.job[a.jid[v]];
+            job = a.jid[v];
+            const JobInfo& J = a.job[job];
             k = J.k;
             row = a.G + row_of(J, v);
+            // after the scatter, cursor[c] is one past the cluster's last member
+            const long long end = a.cursor[c], first = end - a.size[c];
+            whole = first >= wb && end <= wb + 32;
+            if (whole) seg_end = (int)(end - wb);
+            S = a.summ + row_of(J, c);
         }
+        const bool head = whole && (m == (long long)a.cursor[c] - a.size[c]);
         for (int i = 0; i < a.kmax; ++i) {
             const bool on = valid && i < k;
-            const unsigned long long key = on ? ckey(c, row[i]) : kEmpty;
+            const int g = on ? row[i] : 0;
+            const unsigned long long key = on ? ckey(c, g) : kEmpty;
             const unsigned same = __match_any_sync(0xffffffffu, key);
+            const int cnt = __popc(same);
+            const bool leader = on && (__ffs(same) - 1) == lane;
             bool ins = false;
-            if (on && (__ffs(same) - 1) == lane) {
-                if (table_build_add(a.table, mask, key, __popc(same), &ins) < 0) set_err(st, CC_ERR_TABLE_FULL);
+            if (leader) {
+                if (table_build_add(a.table, mask, key, cnt, &ins, whole ? 1 : 0) < 0) set_err(st, CC_ERR_TABLE_FULL);
+                if (ev && whole) acc.add(job, -2LL * cnt * cnt);
             }
             used += __popc(__ballot_sync(0xffffffffu, ins));
+            // summary entry of a whole cluster: the two largest (count, label)
+            const unsigned long long mine =
+                (whole && on) ? ((unsigned long long)(unsigned)cnt << 32) | (unsigned)g : 0ull;
+            const unsigned long long top1 = segment_max(mine, lane, seg_end);
+            const int hl = whole ? (int)((long long)a.cursor[c] - a.size[c] - wb) : lane;
+            const unsigned long long t1 = __shfl_sync(0xffffffffu, top1, hl);
+            const unsigned long long other = (mine != 0 && (unsigned)mine != (unsigned)t1) ? mine : 0ull;
+            const unsigned long long top2 = segment_max(other, lane, seg_end);
+            if (head && on) {
+                const int d2 = top2 ? (int)(unsigned)top2 : -1, m2 = (int)(top2 >> 32);
+                S[i] = make_int4((int)(unsigned)top1, (int)(top1 >> 32), d2, m2);
+            }
         }
     }
     // one add per block: st->used is a single word that every block updates
     if (lane == 0 && used) atomicAdd(&s_used, used);
+    if (ev) job_acc_finish(acc, a.jobs);
     __syncthreads();
     if (threadIdx.x == 0 && s_used) atomicAdd(&st->used, s_used);
 }
 
-// Summary rows of the rebuilt table.  A row entry is read as one unsigned
-// 64-bit value (count << 32 | label id), so an atomic maximum over the slots
-// of a (cluster, partition) leaves the most frequent label and its count
-// (ties to the larger id).
+// Summary rows of the rebuilt table for the keys the build left unmarked
+// (clusters spread over several warps).  Each half of a row entry reads as
+// one unsigned 64-bit value (count << 32 | label id); every such slot offers
+// its (count, label) to the entry, which keeps the two largest by a 16-byte
+// compare-and-swap (ties to the larger id; cleared entries hold count 0 and
+// label -1, below any real key).  Content does not depend on the order of
+// the offers.  Marked slots only get their mark cleared.
 // With eval set (the first rebuild of a heavy sweep) this pass also adds
-// -2 sum n^2 over the new keys to each job's recompute (the table part of F').
+// -2 sum n^2 over the unmarked keys to each job's recompute (the table part
+// of F'; the build added the marked ones).
 __global__ void k_summ_top(SweepArgs a, int conditional, int eval)
 {
     extern __shared__ long long dyn_jobs[];
@@ -433,11 +488,29 @@ __global__ void k_summ_top(SweepArgs a, int conditional, int eval)
         const ulonglong2 e = reinterpret_cast<const ulonglong2*>(a.table)[s];
         const int cnt = (int)(unsigned)(e.y & 0xffffffffull);
         if (e.x == kEmpty || cnt <= 0) continue;
+        if ((e.y >> 32) != 0) {
+            a.table[s].dlt = 0;  // summary and F' part done by the build
+            continue;
+        }
         const int x = (int)(e.x >> 32), g = (int)(unsigned)(e.x & 0xffffffffull);
         const int job = a.jid[x];
         const JobInfo& J = a.job[job];
-        atomicMax(reinterpret_cast<unsigned long long*>(a.summ + row_of(J, x) + (g >> J.lshift)),
-                  ((unsigned long long)(unsigned)cnt << 32) | (unsigned)g);
+        int4* E = a.summ + row_of(J, x) + (g >> J.lshift);
+        const unsigned long long kn = ((unsigned long long)(unsigned)cnt << 32) | (unsigned)g;
+        const volatile unsigned long long* Ev = reinterpret_cast<const volatile unsigned long long*>(E);
+        ulonglong2 cur = make_ulonglong2(Ev[0], Ev[1]);
+        // lock-free: every failed swap means another offer went in; bounded
+        // all the same
+        for (int tries = 0; kn > cur.y; ++tries) {
+            if (tries >= (1 << 20)) {
+                set_err(st, CC_ERR_INVALID);
+                break;
+            }
+            const ulonglong2 nv = kn > cur.x ? make_ulonglong2(kn, cur.x) : make_ulonglong2(cur.x, kn);
+            const ulonglong2 old = entry_cas(E, cur, nv);
+            if (old.x == cur.x && old.y == cur.y) break;
+            cur = old;
+        }
         if (ev) acc.add(job, -2LL * cnt * cnt);
     }
     if (ev) job_acc_finish(acc, a.jobs);
@@ -483,7 +556,160 @@ __global__ void k_zero_recompute(SweepArgs a)
         a.js[j].recompute = 0;
 }
 
+// ---- colouring (colour_batched) ------------------------------------------
+// Priority of a job-local vertex id: the first output of splitmix64 (Steele,
+// Lea and Flood) seeded with it; a bijection, so priorities are distinct.
+__device__ __forceinline__ unsigned long long colour_priority(unsigned long long v)
+{
+    unsigned long long z = v + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_colour_init(ColourArgs a)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) a.colour[v] = -1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.flag = 0;
+}
+
+// One Jones-Plassmann round: an uncoloured vertex whose higher-priority
+// neighbours are all coloured takes the least colour none of them has, which
+// is what the greedy colouring in decreasing priority gives it.  A colour, once
+// written, is final, so a vertex that sees a neighbour coloured in this same
+// round sees its final colour.  *flag counts the vertices left uncoloured.
+__global__ void k_colour_round(ColourArgs a)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const volatile int* colour = a.colour;
+    int left = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
+        if (colour[v] >= 0) continue;
+        const long long vo = a.job[a.jid[v]].vo;
+        const unsigned long long pv = colour_priority((unsigned long long)(v - vo));
+        const long long e0 = a.off[v], e1 = a.off[v + 1];
+        bool ready = true;
+        for (long long e = e0; e < e1 && ready; ++e) {
+            const int u = a.col[e];
+            if (u != v && colour_priority((unsigned long long)(u - vo)) > pv && colour[u] < 0) ready = false;
+        }
+        if (!ready) {
+            ++left;
+            continue;
+        }
+        // least colour not held by a higher-priority neighbour, 64 at a time
+        for (int base = 0;; base += 64) {
+            unsigned long long used = 0;
+            for (long long e = e0; e < e1; ++e) {
+                const int u = a.col[e];
+                if (u == v || colour_priority((unsigned long long)(u - vo)) <= pv) continue;
+                const int cu = colour[u] - base;
+                if (cu >= 0 && cu < 64) used |= 1ull << cu;
+            }
+            if (~used) {
+                a.colour[v] = base + __ffsll((long long)~used) - 1;
+                break;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) left += __shfl_xor_sync(0xffffffffu, left, o);
+    if ((threadIdx.x & 31) == 0 && left) atomicAdd(a.flag, left);
+}
+
+__global__ void k_colour_max(ColourArgs a)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    int m = -1;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) m = max(m, a.colour[v]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(a.flag, m + 1);
+}
+
+// Per class: vertices (cnt[c]) and CSR entries (cnt[classes + 1 + c]).
+__global__ void k_colour_count(ColourArgs a, int classes)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
+        const int c = a.colour[v];
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.cnt + c), 1ull);
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.cnt + classes + 1 + c),
+                  (unsigned long long)(a.off[v + 1] - a.off[v]));
+    }
+}
+
+// Lists the vertices and the CSR entries of each class (cnt now holds the
+// running positions; the order inside a class does not matter).
+__global__ void k_colour_place(ColourArgs a, int classes)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
+        const int c = a.colour[v];
+        const long long d = a.off[v + 1] - a.off[v];
+        const long long p = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(a.cnt + c), 1ull);
+        a.vlist[p] = (int)v;
+        const long long q = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(a.cnt + classes + 1 + c),
+                                                 (unsigned long long)d);
+        for (long long t = 0; t < d; ++t) a.eidx[q + t] = (int)(a.off[v] + t);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_colouring(const ColourArgs& a, int* classes, cudaStream_t s)
+{
+    const int g = grid_for(a.n);
+    k_colour_init<<<g, kSetupBlock, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    // rounds until every vertex is coloured; each round colours at least the
+    // uncoloured vertex of highest priority, so n rounds always suffice
+    for (long long round = 0; e == cudaSuccess; ++round) {
+        if (round > a.n) return cudaErrorUnknown;
+        e = cudaMemsetAsync(a.flag, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        k_colour_round<<<g, kSetupBlock, 0, s>>>(a);
+        int left = 0;
+        e = cudaMemcpyAsync(&left, a.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        if (left == 0) break;
+    }
+    e = cudaMemsetAsync(a.flag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_colour_max<<<g, kSetupBlock, 0, s>>>(a);
+    int nc = 0;
+    e = cudaMemcpyAsync(&nc, a.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (nc < 1) nc = 1;
+    e = cudaMemsetAsync(a.cnt, 0, sizeof(long long) * 2 * ((size_t)nc + 1), s);
+    if (e != cudaSuccess) return e;
+    k_colour_count<<<g, kSetupBlock, 0, s>>>(a, nc);
+    std::vector<long long> cnt(2 * ((size_t)nc + 1));
+    e = cudaMemcpyAsync(cnt.data(), a.cnt, sizeof(long long) * cnt.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    // class offsets: exclusive prefix sums of the counts
+    std::vector<int> voff((size_t)nc + 1, 0);
+    std::vector<long long> eoff((size_t)nc + 1, 0), pos(2 * ((size_t)nc + 1), 0);
+    for (int c = 0; c < nc; ++c) {
+        voff[c + 1] = voff[c] + (int)cnt[c];
+        eoff[c + 1] = eoff[c] + cnt[nc + 1 + c];
+        pos[c] = voff[c];
+        pos[nc + 1 + c] = eoff[c];
+    }
+    e = cudaMemcpyAsync(a.voff, voff.data(), sizeof(int) * voff.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a.eoff, eoff.data(), sizeof(long long) * eoff.size(),
+                                              cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(a.cnt, pos.data(), sizeof(long long) * pos.size(),
+                                              cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_colour_place<<<g, kSetupBlock, 0, s>>>(a, nc);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // pos, voff, eoff are host vectors
+    *classes = nc;
+    return e;
+}
 
 cudaError_t launch_assemble(const AssemblyArgs& a, cudaStream_t s)
 {
@@ -502,10 +728,15 @@ cudaError_t launch_assemble_edges(const AssemblyArgs& a, cudaStream_t s)
 
 cudaError_t launch_compact_labels(const LabelArgs& a, cudaStream_t s)
 {
-    LSlot* m = static_cast<LSlot*>(a.lmap);
-    const unsigned long long cap = a.lmask + 1;
     cudaError_t e = cudaMemsetAsync(a.G, 0xff, sizeof(int) * (size_t)a.rows, s);
     if (e != cudaSuccess) return e;
+    return launch_label_kernels(a, s);
+}
+
+cudaError_t launch_label_kernels(const LabelArgs& a, cudaStream_t s)
+{
+    LSlot* m = static_cast<LSlot*>(a.lmap);
+    const unsigned long long cap = a.lmask + 1;
     k_lmap_clear<<<grid_for((long long)cap), kSetupBlock, 0, s>>>(m, cap);
     k_label_insert<<<grid_for(a.total), kSetupBlock, 0, s>>>(a);
     k_label_assign<<<grid_for(a.total), kSetupBlock, 0, s>>>(a);
@@ -541,7 +772,7 @@ cudaError_t launch_table_rebuild(const SweepArgs& a, long long rows, bool condit
     k_scan_sums<<<1, 1024, 0, s>>>(a, nb, c);
     k_scan_write<<<nb, 1024, 0, s>>>(a, c);
     k_members_scatter<<<grid_for(a.n), kSetupBlock, 0, s>>>(a, c);
-    k_table_build<<<grid_for(a.n), kSetupBlock, 0, s>>>(a, c);
+    k_table_build<<<grid_for(a.n), kSetupBlock, eval ? smem_jobs_bytes(a.jobs) : 0, s>>>(a, c, eval ? 1 : 0);
     k_summ_top<<<grid_for((long long)a.mask_max + 1), kSetupBlock, eval ? smem_jobs_bytes(a.jobs) : 0, s>>>(a, c,
                                                                                                  eval ? 1 : 0);
     k_table_done<<<1, 1, 0, s>>>(a.st, c);

@@ -82,6 +82,7 @@ __global__ void k_run_begin(SweepArgs a, int limit)
         st->run_limit = limit;
         st->run_bodies = 0;
         st->all_active = 1;
+        st->cls = 0;
     }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.jobs; j += gridDim.x * blockDim.x) {
         a.js[j].stop = 0;
@@ -125,65 +126,55 @@ __device__ __forceinline__ int group_sum(int x, int gs)
 
 // The partitions of a job are scored four at a time ("quads"): partition
 // 4q + t is component t of quad q of v's label row (one int4 load) and entry
-// 4q + t of x's summary row (two int4 loads of {d, m} pairs).  Rows are kp =
-// k rounded up to 4 entries, so only the last quad can hold padding, which
-// is masked out (4q + t >= k).  Lane l of a group takes quads l, l + gs, ...
+// 4q + t of x's summary row (one int4 {d1, m1, d2, m2} per partition).  Rows
+// are kp = k rounded up to 4 entries, so only the last quad can hold padding,
+// which is masked out (4q + t >= k).  Lane l of a group takes quads l,
+// l + gs, ...
 
-// Adds partition t of a quad to the summary sums.
-__device__ __forceinline__ void summary_one(int g, int d, int m, bool on, int sx, int& ex, int& ub)
+// Adds one partition to the summary sums: v's label g against the entry e =
+// {d1, m1, d2, m2} of a cluster of size sx.
+__device__ __forceinline__ void summary_one(int g, int4 e, bool on, int sx, int& ex, int& ub)
 {
     if (!on) return;
-    const bool eq = g == d;
-    ex += eq ? m : 0;
-    ub += eq ? m : sx - m;
+    const int m = g == e.x ? e.y : (g == e.z ? e.w : 0);
+    ex += m;
+    // a label other than d1, d2 has at most sx - m1 - m2 members (none when
+    // the two cover the cluster)
+    ub += (g == e.x || g == e.z) ? m : sx - e.y - e.w;
 }
 
 // Summary part of A_x(v) for a non-singleton cluster x (size sx) of job J:
-// ex = sum of m where v carries the row's label d (exact there), ub = ex +
-// sum of (sx - m) elsewhere: the members not carrying d bound the count of
-// any other label, so ub is an upper bound on A_x.
+// ex = the counts of v's labels where they are one of the row's two labels
+// (exact there; 0, also exact, where the two cover the cluster), ub = ex +
+// sum of (sx - m1 - m2) over the other partitions, an upper bound on A_x.
 __device__ __forceinline__ void summary_part(const SweepArgs& a, const JobInfo& J, const int* __restrict__ gv, int x,
                                              int sx, int l, int gs, int& ex, int& ub)
 {
     ex = 0;
     ub = 0;
     const int4* G4 = reinterpret_cast<const int4*>(gv);
-    const int4* S4 = reinterpret_cast<const int4*>(a.summ + row_of(J, x));
+    const int4* S4 = a.summ + row_of(J, x);
     const int kq = J.kp >> 2, k = J.k;
-    constexpr int kQuads = 2;  // quads per lane in flight
-    for (int q0 = l; q0 < kq; q0 += gs * kQuads) {
-        int4 g[kQuads], s0[kQuads], s1[kQuads];
-#pragma unroll
-        for (int b = 0; b < kQuads; ++b) {
-            const int q = q0 + b * gs;
-            g[b] = make_int4(-1, -1, -1, -1);
-            s0[b] = make_int4(-2, 0, -2, 0);
-            s1[b] = s0[b];
-            if (q < kq) {
-                g[b] = __ldg(G4 + q);
-                s0[b] = __ldg(S4 + 2 * q);
-                s1[b] = __ldg(S4 + 2 * q + 1);
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < kQuads; ++b) {
-            const int i = 4 * (q0 + b * gs);
-            summary_one(g[b].x, s0[b].x, s0[b].y, i < k, sx, ex, ub);
-            summary_one(g[b].y, s0[b].z, s0[b].w, i + 1 < k, sx, ex, ub);
-            summary_one(g[b].z, s1[b].x, s1[b].y, i + 2 < k, sx, ex, ub);
-            summary_one(g[b].w, s1[b].z, s1[b].w, i + 3 < k, sx, ex, ub);
-        }
+    for (int q = l; q < kq; q += gs) {
+        const int4 g = __ldg(G4 + q);
+        const int4 e0 = __ldg(S4 + 4 * q), e1 = __ldg(S4 + 4 * q + 1), e2 = __ldg(S4 + 4 * q + 2),
+                   e3 = __ldg(S4 + 4 * q + 3);
+        const int i = 4 * q;
+        summary_one(g.x, e0, i < k, sx, ex, ub);
+        summary_one(g.y, e1, i + 1 < k, sx, ex, ub);
+        summary_one(g.z, e2, i + 2 < k, sx, ex, ub);
+        summary_one(g.w, e3, i + 3 < k, sx, ex, ub);
     }
 }
 
-// Starts the probe of partition t of a quad if the summary leaves it open (v
-// does not carry the row's label and some member of x does not carry it
-// either): the key, its first slot and that slot's contents.
+// Starts the probe of one partition if the summary leaves it open (v carries
+// neither of the row's labels and the two do not cover x): the key, its
+// first slot and that slot's contents.
 __device__ __forceinline__ bool probe_start(const Slot* __restrict__ table, unsigned long long mask, int x, int g,
-                                            int d, int m, bool on, int sx, unsigned long long& key,
-                                            unsigned long long& h, ulonglong2& ev)
+                                            int4 e, bool on, int sx, unsigned long long& key, unsigned long long& h,
+                                            ulonglong2& ev)
 {
-    if (!on || g == d || sx <= m) return false;
+    if (!on || g == e.x || g == e.z || sx <= e.y + e.w) return false;
     key = ckey(x, g);
     h = hash_key(key) & mask;
     ev = __ldg(reinterpret_cast<const ulonglong2*>(table + h));
@@ -197,21 +188,19 @@ __device__ __forceinline__ int probe_part(const SweepArgs& a, const JobInfo& J, 
                                           int gs)
 {
     const int4* G4 = reinterpret_cast<const int4*>(gv);
-    const int4* S4 = reinterpret_cast<const int4*>(a.summ + row_of(J, x));
+    const int4* S4 = a.summ + row_of(J, x);
     const int kq = J.kp >> 2, k = J.k;
     int acc = 0;
     for (int q = l; q < kq; q += gs) {
         const int4 g = __ldg(G4 + q);
-        const int4 s0 = __ldg(S4 + 2 * q);
-        const int4 s1 = __ldg(S4 + 2 * q + 1);
         const int i = 4 * q;
         unsigned long long key[4] = {0, 0, 0, 0}, h[4] = {0, 0, 0, 0};
         ulonglong2 ev[4];
         bool on[4];
-        on[0] = probe_start(table, mask, x, g.x, s0.x, s0.y, i < k, sx, key[0], h[0], ev[0]);
-        on[1] = probe_start(table, mask, x, g.y, s0.z, s0.w, i + 1 < k, sx, key[1], h[1], ev[1]);
-        on[2] = probe_start(table, mask, x, g.z, s1.x, s1.y, i + 2 < k, sx, key[2], h[2], ev[2]);
-        on[3] = probe_start(table, mask, x, g.w, s1.z, s1.w, i + 3 < k, sx, key[3], h[3], ev[3]);
+        on[0] = probe_start(table, mask, x, g.x, __ldg(S4 + 4 * q), i < k, sx, key[0], h[0], ev[0]);
+        on[1] = probe_start(table, mask, x, g.y, __ldg(S4 + 4 * q + 1), i + 1 < k, sx, key[1], h[1], ev[1]);
+        on[2] = probe_start(table, mask, x, g.z, __ldg(S4 + 4 * q + 2), i + 2 < k, sx, key[2], h[2], ev[2]);
+        on[3] = probe_start(table, mask, x, g.w, __ldg(S4 + 4 * q + 3), i + 3 < k, sx, key[3], h[3], ev[3]);
 #pragma unroll
         for (int b = 0; b < 4; ++b)
             if (on[b]) acc += resolve(table, mask, key[b], h[b], ev[b]);
@@ -289,17 +278,25 @@ __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
     const long long groups = (long long)gridDim.x * blockDim.x / gs;
     const JobInfo J0 = a.job[0];
     const int all = st->all_active, last = st->stamp - 1;
-    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x - lane) / gs; base < a.n;
+    // colour_batched: only the vertices of the current class, listed in vlist
+    long long count = a.n, vbase = 0;
+    if (a.colour_mode) {
+        vbase = a.voff[st->cls];
+        count = a.voff[st->cls + 1] - vbase;
+    }
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x - lane) / gs; base < count;
          base += groups) {
-        const long long v = base + lane / gs;
-        const bool valid = v < a.n;
+        const long long idx = base + lane / gs;
+        const bool valid = idx < count;
+        const long long v = a.colour_mode ? (valid ? (long long)__ldg(a.vlist + vbase + idx) : 0) : idx;
         const int j = (kSingle || !valid) ? 0 : __ldg(a.jid + v);
         const bool run = valid && (kSingle || !a.js[j].stop);
         const int cv = run ? __ldg(a.C + v) : 0;
         // A_a is a function of v's cluster alone: it is recomputed only when
         // a vertex moved into or out of that cluster in the previous sweep
-        // (or in a run's first sweep), and kept in aown[] otherwise
-        const bool own = run && (all || a.chg[cv] == last);
+        // (or in a run's first sweep), and kept in aown[] otherwise; a colour
+        // class was last scored several bodies ago, so it always recomputes
+        const bool own = run && (a.colour_mode || all || a.chg[cv] == last);
         const bool on = own;
         if (a.active_set && run && l == 0) {
             // active set: every candidate again if a or the previous bid's
@@ -370,20 +367,29 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
     const int all = st->all_active, last = st->stamp - 1;
     const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
     constexpr long long span = 32 * kChunks;
-    for (long long base = ((long long)blockIdx.x * kWarpsPerBlock + w) * span; base < a.nnz; base += nwarps * span) {
+    // colour_batched: only the CSR entries of the current class's vertices,
+    // listed in eidx
+    long long count = a.nnz, ebase = 0;
+    if (a.colour_mode) {
+        ebase = a.eoff[st->cls];
+        count = a.eoff[st->cls + 1] - ebase;
+    }
+    for (long long base = ((long long)blockIdx.x * kWarpsPerBlock + w) * span; base < count; base += nwarps * span) {
         // singleton candidates fill the scratch from the front, the others
         // from the back, so that scoring rounds take one path each
         int ns = 0, nt = 0;
         for (int c = 0; c < kChunks; ++c) {
-            const long long e = base + c * 32 + lane;
+            const long long ep = base + c * 32 + lane;
+            long long e = ep;
             int v = 0, u = 0, x = -1, j = 0, cv = 0;
-            if (e < a.nnz) {
+            if (ep < count) {
+                if (a.colour_mode) e = __ldg(a.eidx + ebase + ep);
                 v = __ldg(a.src + e);
                 if (!kSingle) j = __ldg(a.jid + v);
             }
             // entries of stopped jobs are not scored; a chunk of only such
             // entries is skipped whole
-            const bool live = e < a.nnz && (kSingle || !a.js[j].stop);
+            const bool live = ep < count && (kSingle || !a.js[j].stop);
             if (__all_sync(kFull, !live)) continue;
             if (live) {
                 u = __ldg(a.col + e);
@@ -987,19 +993,33 @@ __global__ void k_end_jobs(SweepArgs a)
         JobState& s = a.js[j];
         if (s.stop) continue;
         if (s.mode != 0) s.F += s.dF;
-        if (s.sweeps < a.hist_cap) {
-            cc_sweep_info r;
-            r.proposals = (int64_t)s.nprop;
-            r.p1 = (int64_t)s.np1;
-            r.dF_p1 = s.dF_p1;
-            r.fallback = s.mode == 2 ? 1 : 0;
-            r.moves = (int64_t)s.moves;
-            r.F = s.F;
-            a.hist[(long long)j * a.hist_cap + s.sweeps] = r;
+        cc_sweep_info r;
+        r.proposals = (int64_t)s.nprop;
+        r.p1 = (int64_t)s.np1;
+        r.dF_p1 = s.dF_p1;
+        r.fallback = s.mode == 2 ? 1 : 0;
+        r.moves = (int64_t)s.moves;
+        r.F = s.F;
+        if (a.colour_mode) {
+            // a colour class: add it to the sweep's totals; the sweep ends
+            // with its last class
+            s.t_prop += r.proposals;
+            s.t_p1 += r.p1;
+            s.t_dFp1 += r.dF_p1;
+            s.t_fb += r.fallback;
+            s.t_moves += r.moves;
+            if (st->cls + 1 < st->ncls) continue;
+            r.proposals = s.t_prop;
+            r.p1 = s.t_p1;
+            r.dF_p1 = s.t_dFp1;
+            r.fallback = s.t_fb;
+            r.moves = s.t_moves;
+            s.t_prop = s.t_p1 = s.t_dFp1 = s.t_fb = s.t_moves = 0;
         }
+        if (s.sweeps < a.hist_cap) a.hist[(long long)j * a.hist_cap + s.sweeps] = r;
         s.sweeps += 1;
         s.run_sweeps += 1;
-        if (s.nprop == 0 || s.run_sweeps >= st->run_limit) s.stop = 1;
+        if (r.proposals == 0 || s.run_sweeps >= st->run_limit) s.stop = 1;
         else atomicAdd(&st->active, 1);
     }
 }
@@ -1033,7 +1053,13 @@ __global__ void k_end(SweepArgs a)
         return;
     }
     st->all_active = 0;
-    st->stop = st->active == 0 ? 1 : 0;
+    if (a.colour_mode && st->cls + 1 < st->ncls) {
+        st->cls += 1;  // the sweep goes on with the next colour class
+        st->stop = 0;
+    } else {
+        st->cls = 0;
+        st->stop = st->active == 0 ? 1 : 0;
+    }
     // compaction: rebuild without the dead keys when occupied slots pass one
     // half of the capacity; the new capacity holds the live keys plus k x
     // (proposals of this sweep), a forecast of the next sweep's new keys, at

@@ -269,3 +269,19 @@ def test_batch_empty_moves(cc):
             r = oracle.sync_run(ro, col, lab, 30, C0=C0[j], empty=True)
             assert b.history(j) == r.stats
             np.testing.assert_array_equal(ids[b.offsets[j]:b.offsets[j + 1]], r.C)
+
+
+def test_batch_colour_batched(cc):
+    """Colour-batched sweeps over a batch: jobs with different numbers of
+    colour classes run the classes in lockstep; each job equals the oracle's
+    colour-batched run of that job alone."""
+    jobs = _mixed_jobs(5, 525)
+    o = cc.cc_default_options()
+    o.colour_batched = 1
+    with cc.ConsensusBatch(jobs, o) as b:
+        b.run_until_converged(20)
+        ids = b.cluster_ids()
+        for j, (ro, col, lab) in enumerate(jobs):
+            r = oracle.colour_run(ro, col, lab, 20)
+            assert b.history(j) == r.stats
+            np.testing.assert_array_equal(ids[b.offsets[j]:b.offsets[j + 1]], r.C)

@@ -560,3 +560,42 @@ def test_empty_moves_golden(cc):
             info = job.sweep()
             assert info == {key: want[key] for key in info}
             np.testing.assert_array_equal(job.cluster_ids(), want["C"])
+
+
+# ------------------------------------------- colour-batched variant (option)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_colour_batched_runs(cc, mode):
+    """cc_options.colour_batched: every sweep record (sums over the colour
+    classes), the raw ids and F equal the oracle's colour-batched run, on the
+    small SBM, an LFR-style graph with hubs and a kNN graph, in every sweep
+    mode; with the move-to-empty variant too on one of them."""
+    cases = [(make_config("sbm"), False),
+             (make_config("lfr", n=20000, k=8, cmin=20, cmax=1000, max_deg=1000, seed=11), False),
+             (make_config("knn", n=6000, comps=30, dim=20, k=12, seed=21), True)]
+    for c, empty in cases:
+        ro, col, lab = c["row_off"], c["col"], c["labels"]
+        ref = oracle.colour_run(ro, col, lab, 20, empty=empty)
+        assert_same(gpu_run(cc, ro, col, lab, 20, sweep_mode=mode, colour_batched=1,
+                            empty_moves=1 if empty else 0), ref)
+
+
+def test_colour_batched_stepwise_and_warm_start(cc):
+    """One sweep at a time (cc_sweep runs every class once) from a random
+    warm start, against the oracle sweep by sweep; then a reset repeats the
+    run from the singleton start."""
+    c = make_config("lfr", n=5003, k=37, cmin=20, cmax=1000, max_deg=1000, seed=12)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    rng = np.random.default_rng(3)
+    C0 = _random_grouping(rng, 5003, 200)
+    ref = oracle.colour_run(ro, col, lab, 25, C0=C0)
+    with cc.Consensus(ro, col, lab, options(cc, colour_batched=1)) as job:
+        job.set_cluster_ids(C0)
+        for want in ref.stats:
+            assert job.sweep() == want
+        np.testing.assert_array_equal(job.cluster_ids(), ref.C)
+        job.reset()
+        ref2 = oracle.colour_run(ro, col, lab, 20)
+        assert job.run_until_converged(20) == ref2.sweeps
+        assert job.history() == ref2.stats

@@ -170,3 +170,75 @@ def test_estimate_covers_allocation(cc):
         held = free0 - free1
         assert 0.9 * est <= held <= est + (64 << 20)
         job.run_until_converged(20)
+
+
+def _sweeps_and_job(seed, n, kind, k):
+    d = make_job(np.random.default_rng(seed), n, kind, k)
+    job = (d["row_off"], d["col"], d["labels"])
+    return oracle.sync_run(*job, 20), job
+
+
+def test_serve_releases_a_job_before_its_slowest_sibling(cc):
+    """Two jobs of one context (same lane bin, sizes within a factor 4), one
+    needing several sweeps fewer than the other: the short one is reported
+    done while the context still runs the long one, and both equal the
+    oracle's runs."""
+    short = long_ = None
+    for seed in range(200):
+        ref, job = _sweeps_and_job(1000 + seed, 1500, "lfr" if seed % 2 else "sbm", 6)
+        if short is None or ref.sweeps < short[0].sweeps:
+            short = (ref, job)
+        if long_ is None or ref.sweeps > long_[0].sweeps:
+            long_ = (ref, job)
+        if long_[0].sweeps - short[0].sweeps >= 4:
+            break
+    assert long_[0].sweeps - short[0].sweeps >= 4  # a graph launch runs 4 sweeps
+    with cc.Server(max_active=1, max_batch_jobs=4) as srv:
+        t_long = srv.submit(*long_[1])
+        t_short = srv.submit(*short[1])
+        seen = {}
+        calls = 0
+        while len(seen) < 2:
+            done, _ = srv.progress(wait=True)
+            calls += 1
+            st = srv.stats()
+            for t in done:
+                seen[t] = (calls, st["in_flight"])
+            assert calls < 10000
+        assert srv.stats()["batches"] == 1  # both ran in one context
+        assert seen[t_short][0] < seen[t_long][0]
+        assert seen[t_short][1] == 1  # the context was still in flight
+        for t, (ref, _) in ((t_short, short), (t_long, long_)):
+            r = srv.result(t)
+            assert r["status"] == 0 and r["sweeps"] == ref.sweeps and r["F"] == ref.F
+            np.testing.assert_array_equal(r["labels"], oracle.renumber(ref.C))
+
+
+def test_serve_loads_a_waiting_job_into_a_running_context(cc):
+    """One context of two jobs (max_active 1): when its short job stops, a
+    waiting job of the same lane bin that fits the short job's place is
+    loaded into it while the long job keeps running (no new context), and
+    every job equals the oracle's run of it alone.  The loaded job is
+    smaller than the place, so the place's unused vertices and CSR entries
+    are exercised."""
+    cands = []
+    for seed in range(200):
+        ref, job = _sweeps_and_job(2000 + seed, 1500, "lfr" if seed % 2 else "sbm", 6)
+        cands.append((ref, job))
+    cands.sort(key=lambda rj: rj[0].sweeps)
+    short, long_ = cands[0], cands[-1]
+    assert long_[0].sweeps - short[0].sweeps >= 4
+    ref_w, job_w = _sweeps_and_job(4242, 900, "lfr", 5)  # fewer vertices, edges, partitions
+    assert len(job_w[0]) - 1 < len(short[1][0]) - 1 and len(job_w[1]) <= len(short[1][1])
+    with cc.Server(max_active=1, max_batch_jobs=2) as srv:
+        t_long = srv.submit(*long_[1])
+        t_short = srv.submit(*short[1])
+        srv.progress()  # both admitted into one context
+        t_w = srv.submit(*job_w)
+        srv.drain()
+        st = srv.stats()
+        assert st["batches"] == 1 and st["admitted_running"] == 1, st
+        for t, ref in ((t_long, long_[0]), (t_short, short[0]), (t_w, ref_w)):
+            r = srv.result(t)
+            assert r["status"] == 0 and r["sweeps"] == ref.sweeps and r["F"] == ref.F, (t, r["F"], ref.F)
+            np.testing.assert_array_equal(r["labels"], oracle.renumber(ref.C))
