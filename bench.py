@@ -529,6 +529,16 @@ def single_job(args, c, local, dist, rank, world, extras=True):
     return out
 
 
+def autotune_record(ccg):
+    """Lane counts the library's autotuner chose per lane bin (k 1..10,
+    11..20, 21..40, 41..80, 81..160, above; 0: not tuned)."""
+    import ctypes
+
+    rec = (ctypes.c_int32 * 6)()
+    ccg._native._check(ccg._native.lib.cc_autotune_record(6, rec), None)
+    return {b: int(rec[i]) for i, b in enumerate(["1-10", "11-20", "21-40", "41-80", "81-160", "161-"]) if rec[i]}
+
+
 def mix_pool(args, kind):
     """Specs of the batched / served mix, the pool job each spec draws, and the pool."""
     from workloads.configs import batch_job_specs, serve_job_specs
@@ -568,6 +578,7 @@ def run_batch(args, world, local, specs, member, pool, gen_s):
     sizes = [(len(ro) - 1, len(col), lab.shape[0]) for ro, col, lab in jobs]
     opts = ccg.cc_default_options()
     opts.active_set = 1  # jobs/s: re-score only the active set (identical results)
+    opts.autotune = 1    # lanes per item timed per lane bin on its first context (identical results)
     budget = int(torch.cuda.mem_get_info()[0] * args.budget_frac)
     batch_of, nb = ccg._native.cc_plan_batches(sizes, budget, 0, opts)
     waves = [[] for _ in range(nb)]
@@ -633,7 +644,8 @@ def run_batch(args, world, local, specs, member, pool, gen_s):
     cfg = mix_config("batch", specs, member, pool, gen_s)
     cfg.update({"batches": nb, "jobs_per_batch": [len(w) for w in waves], "budget_bytes": budget,
                 "planner": "cc_plan_batches: lane bins of k, then batches within the device budget",
-                "options": "active_set = 1 in both arms",
+                "options": "active_set = 1, autotune = 1 in both arms",
+                "autotune_lanes_by_bin": autotune_record(ccg),
                 "l2": "inputs larger than L2, no flush"})
     return {"metric": "batched jobs/s", "value": J / tb, "unit": "jobs/s", "n_gpus": world, "steps": steps,
             "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
@@ -664,6 +676,7 @@ def run_serve(args, world, local, specs, member, pool, gen_s, requests):
     req = [int(m) for m in member[:R]]
     opts = ccg.cc_default_options()
     opts.active_set = 1  # jobs/s: re-score only the active set (identical results)
+    opts.autotune = 1    # lanes per item timed per lane bin on its first context (identical results)
 
     def solo(i):
         with ccg.Consensus(*pool[i], opts) as c:
@@ -732,6 +745,7 @@ def run_serve(args, world, local, specs, member, pool, gen_s, requests):
                 "served": {"jobs_per_s": R / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mismatches": bad,
                            "contexts": st["batches"], "max_in_flight": st["max_in_flight"],
+                           "loaded_into_running_contexts": st["admitted_running"],
                            "peak_bytes": st["peak_bytes"]},
                 "plain": {"jobs_per_s": R / pspan, "p50_ms": 1e3 * float(np.percentile(plat, 50)),
                           "p99_ms": 1e3 * float(np.percentile(plat, 99))}})
@@ -740,8 +754,10 @@ def run_serve(args, world, local, specs, member, pool, gen_s, requests):
     cfg.update({"requests_per_rate": R, "arrivals": "Poisson, seeds 0x5EED + 4 + rate index",
                 "plain_service_rate_jobs_per_s": mu, "server_saturated_jobs_per_s": sat,
                 "rates": "0.5, 0.9, 1.5 x the server's saturated jobs/s (all requests waiting at t = 0)",
-                "server": "cc_server max_active 8, max_batch_jobs 256",
-                "options": "active_set = 1 in both arms"})
+                "server": "cc_server max_active 8, max_batch_jobs 256; jobs released as they stop, waiting jobs "
+                          "loaded into finished places of running contexts",
+                "options": "active_set = 1, autotune = 1 in both arms",
+                "autotune_lanes_by_bin": autotune_record(ccg)})
     return {"metric": "served jobs/s, p50/p99 latency", "value": top["served"]["jobs_per_s"], "unit": "jobs/s",
             "n_gpus": world, "steps": len(rates), "warmup": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg, "rates": results,

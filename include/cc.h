@@ -112,6 +112,13 @@ typedef struct {
                                active_set = 0 and fewer than 2^31 CSR entries per context.
                                cc_last_run_timing then gives one entry per class run.  0
                                (default): the synchronous sweep */
+    int32_t autotune;       /* 1 (with lanes = 0): the first run of the context times its
+                               proposal kernels once for each candidate lane count (the
+                               automatic choice, half and twice it) on the state after the run's
+                               first sweep, and keeps the fastest; the choice is remembered per
+                               device and lane bin (see cc_plan_batches) for the later contexts
+                               of the process, which then skip the timing.  Results are
+                               identical; only speed changes.  0 (default): automatic rule */
 } cc_options;
 
 /* State of the contingency hash of a context. */
@@ -382,7 +389,8 @@ cc_status cc_plan_batches(int32_t jobs, const cc_job_desc* descs, const cc_optio
  * launches of a context, every job of it whose run has stopped is released
  * at once (labels, objective, sweeps), whatever its siblings still do, and
  * a waiting job of the same lane bin that fits the released job's place (no
- * more vertices, CSR entries, partitions or label rows than it) is loaded
+ * more vertices, CSR entries, partitions or label rows than it, and at least
+ * a quarter of its vertices and CSR entries) is loaded
  * into that place and joins the running union from its singleton start
  * (not with colour_batched).  A job's results are those of running it
  * alone.  Single-threaded:
@@ -485,6 +493,12 @@ void cc_server_destroy(cc_server* s);
 #define CC_NOALLOC_MAX_N (1 << 21)
 #define CC_NOALLOC_SCRATCH_INTS (2 * CC_NOALLOC_MAX_N + CC_NOALLOC_MAX_N / 1024 + 64)
 cc_status cc_renumber_noalloc(int32_t n, const int32_t* ids_dev, int32_t* labels_dev, void* stream);
+/* The lane counts the autotuner (cc_options.autotune) chose on the current
+ * device, per lane bin (0: 1..10 partitions, 1: 11..20, 2: 21..40, 3: 41..80,
+ * 4: 81..160, 5: above): out[b] for b < bins (at most 6), 0 where no
+ * context of that bin was tuned yet.  Never fails for a non-null out. */
+cc_status cc_autotune_record(int32_t bins, int32_t* out);
+
 /* CC_NOALLOC_MAX_N as compiled into the library (for bindings that cannot
  * read this header's macros).  Never fails. */
 int32_t cc_noalloc_max_n(void);

@@ -26,7 +26,7 @@ EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", 
            "cc_batch_create", "cc_job_count", "cc_job_objective", "cc_job_history", "cc_job_labels",
            "cc_metrics", "cc_partition_distances", "cc_group_partitions", "cc_estimate_bytes", "cc_plan_batches", "cc_server_default_options", "cc_server_create", "cc_server_submit",
            "cc_server_progress", "cc_server_job", "cc_server_stats", "cc_server_last_error", "cc_server_destroy",
-           "cc_renumber_noalloc", "cc_noalloc_max_n")
+           "cc_renumber_noalloc", "cc_noalloc_max_n", "cc_autotune_record")
 
 
 class CCError(RuntimeError):
@@ -40,7 +40,7 @@ class cc_options(ctypes.Structure):
                 ("table_log2", ctypes.c_int32), ("table_start_log2", ctypes.c_int32),
                 ("sweep_mode", ctypes.c_int32), ("lanes", ctypes.c_int32), ("active_set", ctypes.c_int32),
                 ("no_regions", ctypes.c_int32), ("empty_moves", ctypes.c_int32),
-                ("colour_batched", ctypes.c_int32)]
+                ("colour_batched", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class cc_table_info(ctypes.Structure):
@@ -172,6 +172,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cc_renumber_noalloc.argtypes = [c.c_int32, P, P, P]
     lib.cc_noalloc_max_n.restype = c.c_int32
     lib.cc_noalloc_max_n.argtypes = []
+    lib.cc_autotune_record.restype = c.c_int
+    lib.cc_autotune_record.argtypes = [c.c_int32, P]
     return lib
 
 

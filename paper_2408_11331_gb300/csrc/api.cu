@@ -2,6 +2,7 @@
 // jobs held as one disjoint union), the sweep loop as captured CUDA graphs,
 // and the output calls.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -259,23 +260,100 @@ long long launch_budget(const cc_ctx* c, int limit, int chunk)
     return ((long long)limit * c->ncls + chunk - 1) / chunk + 64;
 }
 
+// Lane counts chosen by the autotuner, per device and lane bin (0 = none yet).
+std::atomic<int> g_tuned[kMaxDevices][6];
+
+int lane_bin(int k)
+{
+    int b = 0;
+    for (int g = lanes_for_k(k); g > 1 && b < 5; g >>= 1) ++b;
+    return b;
+}
+
+// Times the proposal kernels once per candidate lane count on the current
+// state (each twice, the second kept) and keeps the fastest; the cached
+// sweep graphs, which hold the old count, are dropped.
+cc_status tune_lanes(cc_ctx* c)
+{
+    const int base = lanes_for_k(c->kmax);
+    std::vector<int> cands;
+    if (base > 1) cands.push_back(base / 2);
+    cands.push_back(base);
+    if (base < 32) cands.push_back(base * 2);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CC_CUDA(c, cudaEventCreate(&e0));
+    CC_CUDA(c, cudaEventCreate(&e1));
+    std::vector<float> ms(cands.size(), 0.f);
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
+            SweepArgs a = c->args;
+            a.gs = cands[i];
+            e = cudaEventRecord(e0, c->stream);
+            if (e == cudaSuccess) e = launch_propose_probe(a, c->grid, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = launch_clear_bids(a, c->grid, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[i], e0, e1);
+            c->launches += 3;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+    size_t best = 0;
+    for (size_t i = 1; i < cands.size(); ++i)
+        if (ms[i] < ms[best]) best = i;
+    c->args.gs = cands[best];
+    for (auto& kv : c->graphs) destroy_graph(kv.second);
+    c->graphs.clear();
+    if (c->device >= 0 && c->device < kMaxDevices) g_tuned[c->device][lane_bin(c->kmax)].store(cands[best]);
+    return CC_OK;
+}
+
 // Runs every job until it stops; *done = largest number of sweeps of a job in this run.
 cc_status run(cc_ctx* c, int limit, int* done)
 {
-    const int chunk = chunk_bodies(c, limit);
-    RunGraph* g = nullptr;
-    cc_status r = ensure_graph(c, chunk, &g);
-    if (r != CC_OK) return r;
     CC_CUDA(c, launch_run_begin(c->args, limit, c->stream));
     c->launches += 1;
     c->sweep_ms.clear();
     c->propose_ms.clear();
     DevState st;
     int before = 0;
+    cc_status r = CC_OK;
+    if (!c->tuned) {
+        // autotune: the run's first sweep alone, then the lane counts timed
+        // on the state it left
+        RunGraph* g1 = nullptr;
+        r = ensure_graph(c, 1, &g1);
+        if (r != CC_OK) return r;
+        CC_CUDA(c, cudaGraphLaunch(g1->exec, c->stream));
+        c->launches += c->opt.no_regions ? kKernelsPerSweep : kKernelsOutsideRegions;
+        r = read_state(c, &st);
+        if (r != CC_OK) return r;
+        if (st.run_bodies > 0) {
+            float x = 0.f, y = 0.f;
+            CC_CUDA(c, cudaEventElapsedTime(&x, g1->bound[0], g1->bound[1]));
+            CC_CUDA(c, cudaEventElapsedTime(&y, g1->prop[0], g1->prop[1]));
+            c->sweep_ms.push_back(x);
+            c->propose_ms.push_back(y);
+        }
+        before = st.run_bodies;
+        if (!st.stop && !st.err) {
+            r = tune_lanes(c);
+            if (r != CC_OK) return r;
+        }
+        c->tuned = true;
+        limit -= st.run_bodies > 0 ? 1 : 0;
+    }
+    const int chunk = chunk_bodies(c, std::max(limit, 1));
+    RunGraph* g = nullptr;
+    r = ensure_graph(c, chunk, &g);
+    if (r != CC_OK) return r;
     // a sweep abandoned for lack of table space is retried in the next body,
     // so the number of launches is bounded by the limit plus the retries
-    const long long budget = launch_budget(c, limit, chunk);
-    for (long long launch = 0; launch < budget; ++launch) {
+    const long long budget = launch_budget(c, std::max(limit, 1), chunk);
+    for (long long launch = 0; launch < budget && !(before > 0 && (st.stop || st.err)); ++launch) {
         CC_CUDA(c, cudaGraphLaunch(g->exec, c->stream));
         c->launches += (long long)chunk * (c->opt.no_regions ? kKernelsPerSweep : kKernelsOutsideRegions);
         r = read_state(c, &st);
@@ -382,6 +460,7 @@ cc_status check_options(const cc_options& opt, std::string* msg)
     if (opt.colour_batched != 0 && opt.colour_batched != 1)
         return bad(CC_ERR_INVALID, "colour_batched must be 0 or 1");
     if (opt.colour_batched && opt.active_set) return bad(CC_ERR_INVALID, "colour_batched needs active_set = 0");
+    if (opt.autotune != 0 && opt.autotune != 1) return bad(CC_ERR_INVALID, "autotune must be 0 or 1");
     return CC_OK;
 }
 
@@ -694,6 +773,17 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     a.keys = (unsigned long long)keys;
     a.sweep_mode = c->opt.sweep_mode;
     a.gs = c->opt.lanes > 0 ? c->opt.lanes : lanes_for_k(kmax);
+    // autotune: a choice made earlier on this device for the same lane bin is
+    // used as it is; otherwise the first run times the candidates
+    c->tuned = true;
+    if (c->opt.autotune && c->opt.lanes == 0 && !c->opt.colour_batched) {
+        int dev = 0;
+        const int known = (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevices)
+                              ? g_tuned[dev][lane_bin(kmax)].load()
+                              : 0;
+        if (known > 0) a.gs = known;
+        else c->tuned = false;
+    }
     a.active_set = c->opt.active_set;
     a.empty_moves = c->opt.empty_moves;
     a.chg = c->chg;
@@ -877,16 +967,81 @@ __global__ void k_load_csr(long long vo, long long n, long long ncap, long long 
         col[eo + e] = (int)(vo + (e < nnz ? col_in[e] : n - 1));
 }
 
-__global__ void k_load_src(long long vo, long long ncap, const long long* __restrict__ off, int* src)
+// Source vertex of every CSR entry of the place, one thread per entry: the
+// vertex whose row holds it (binary search in the new job's offsets; the
+// unused entries at the end belong to its last vertex).
+__global__ void k_load_src(long long vo, long long n, long long eo, long long nnz, long long nnzcap,
+                           const long long* __restrict__ ro, int* src)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ncap; t += stride)
-        for (long long e = off[vo + t]; e < off[vo + t + 1]; ++e) src[e] = (int)(vo + t);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnzcap; e += stride) {
+        long long v = n - 1;
+        if (e < nnz) {
+            long long lo = 0, hi = n - 1;  // last t with ro[t] <= e
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) >> 1;
+                if (ro[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            v = lo;
+        }
+        src[eo + e] = (int)(vo + v);
+    }
+}
+
+// The finished job's contingency keys (its clusters' ids lie in its place)
+// get count 0 before its state is overwritten; the table stays valid for the
+// other jobs.  Skipped if the table does not hold the counts of C.
+__global__ void k_unload_keys(SweepArgs a, JobInfo J, long long vo)
+{
+    if (!a.st->tvalid) return;
+    const unsigned long long mask = a.st->mask;
+    const long long total = J.n * J.k, stride = (long long)gridDim.x * blockDim.x;
+    long long dead = 0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const long long vl = t / J.k;
+        const int i = (int)(t - vl * J.k);
+        const int g = a.G[J.go + vl * J.kp + i];
+        const long long s = table_find(a.table, mask, ckey(a.C[vo + vl], g));
+        if (s >= 0 && atomicExch(&a.table[s].cnt, 0) > 0) ++dead;
+    }
+    if (dead) atomicAdd(reinterpret_cast<unsigned long long*>(&a.st->live), (unsigned long long)(-dead));
+}
+
+// The new job's singleton keys, count 1 each.  If the table runs short, it is
+// marked as not holding the counts, so that the next sweep rebuilds it.
+__global__ void k_load_keys(SweepArgs a, JobInfo J, long long vo)
+{
+    DevState* st = a.st;
+    if (!st->tvalid) return;
+    const unsigned long long mask = st->mask;
+    const long long total = J.n * J.k, stride = (long long)gridDim.x * blockDim.x;
+    long long live = 0, used = 0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const long long vl = t / J.k;
+        const int i = (int)(t - vl * J.k);
+        bool ins = false;
+        const long long s = table_find_or_insert(a.table, mask, ckey((int)(vo + vl), a.G[J.go + vl * J.kp + i]), &ins);
+        if (s < 0) {
+            st->tvalid = 0;
+            continue;
+        }
+        used += ins ? 1 : 0;
+        if (atomicAdd(&a.table[s].cnt, 1) == 0) ++live;
+    }
+    if (live) atomicAdd(reinterpret_cast<unsigned long long*>(&st->live), (unsigned long long)live);
+    if (used) atomicAdd(&st->used, (unsigned long long)used);
+}
+
+__global__ void k_load_check_fill(DevState* st)
+{
+    const unsigned long long cap = st->mask + 1;
+    if (st->used > cap - (cap >> 3)) st->tvalid = 0;  // past 7/8: rebuild in the next sweep
 }
 
 // Singleton state of the place's vertices (stamped as changed in the sweep
-// just run, so that the next sweep computes their own-cluster sums), the
-// summary rows of the new job's label rows, and a pending table rebuild.
+// just run, so that the next sweep computes their own-cluster sums) and the
+// summary rows of the new job's label rows; the run goes on.
 __global__ void k_load_state(SweepArgs a, long long vo, long long ncap, long long go, long long rows)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -906,10 +1061,7 @@ __global__ void k_load_state(SweepArgs a, long long vo, long long ncap, long lon
         const int g = a.G[go + r];
         a.summ[go + r] = make_int4(g, g >= 0 ? 1 : 0, -1, 0);
     }
-    if (t0 == 0) {
-        a.st->tvalid = 0;  // the next sweep is heavy: the table is rebuilt from C
-        a.st->stop = 0;
-    }
+    if (t0 == 0) a.st->stop = 0;
 }
 
 // Job-local renumbering of one job (vertices vo .. vo + n - 1): first holds,
@@ -1100,8 +1252,11 @@ cc_status ctx_copy_labels(cc_ctx* c, const int* dev_labels, int j, int32_t* out)
 bool ctx_slot_fits(const cc_ctx* c, int j, const JobInput& in)
 {
     const long long kp_new = (in.k + 3) & ~3, kp_cap = (c->slot_k[j] + 3) & ~3;
+    // no larger than the place, and not much smaller: every sweep scans the
+    // whole place, so a small job in a large place would pay for it
     return !c->opt.colour_batched && in.n >= 1 && in.n <= c->slot_n[j] && in.nnz <= c->slot_nnz[j] &&
-           in.k >= 1 && in.k <= c->slot_k[j] && (long long)in.n * kp_new <= c->slot_n[j] * kp_cap &&
+           4LL * in.n >= c->slot_n[j] && 4LL * in.nnz >= c->slot_nnz[j] && in.k >= 1 && in.k <= c->slot_k[j] &&
+           (long long)in.n * kp_new <= c->slot_n[j] * kp_cap &&
            (long long)in.n * in.k <= c->slot_n[j] * (long long)c->slot_k[j] && in.k <= c->kmax;
 }
 
@@ -1180,10 +1335,12 @@ cc_status ctx_load_job(cc_ctx* c, int j, const JobInput& in)
         return fail(c, CC_ERR_INVALID, "malformed CSR: offsets must start at 0, end at nnz and not decrease; "
                                        "columns must lie in [0, n)");
     }
+    // the finished job's keys leave the table
+    k_unload_keys<<<g, 256, 0, c->stream>>>(c->args, c->job[j], J.vo);
     // the graph into the place: offsets, columns (union ids; unused entries
     // become self-loops of the last vertex), job of each vertex, sources
     k_load_csr<<<g, 256, 0, c->stream>>>(J.vo, n, ncap, eo, nnz, nnzcap, ro, col, j, c->jobs, c->off, c->col, c->jid);
-    k_load_src<<<g, 256, 0, c->stream>>>(J.vo, ncap, c->off, c->src);
+    k_load_src<<<g, 256, 0, c->stream>>>(J.vo, n, eo, nnz, nnzcap, ro, c->src);
     // labels: compacted as at creation, into the place's rows
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(c->G + J.go, 0xff, sizeof(int) * (size_t)(n * J.kp), c->stream);
@@ -1211,6 +1368,8 @@ cc_status ctx_load_job(cc_ctx* c, int j, const JobInput& in)
     // table rebuild in the next sweep
     if (e == cudaSuccess) {
         k_load_state<<<g, 256, 0, c->stream>>>(c->args, J.vo, ncap, J.go, n * J.kp);
+        k_load_keys<<<g, 256, 0, c->stream>>>(c->args, J, J.vo);
+        k_load_check_fill<<<1, 1, 0, c->stream>>>(c->st);
         e = cudaGetLastError();
     }
     JobState jsr;
@@ -1285,6 +1444,15 @@ void cc_default_options(cc_options* opt)
     if (!opt) return;
     std::memset(opt, 0, sizeof(*opt));
     opt->max_sweeps = 20;
+}
+
+cc_status cc_autotune_record(int32_t bins, int32_t* out)
+{
+    if (!out) return fail(nullptr, CC_ERR_INVALID, "out is NULL");
+    int dev = 0;
+    const bool ok = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevices;
+    for (int b = 0; b < bins && b < 6; ++b) out[b] = ok ? g_tuned[dev][b].load() : 0;
+    return CC_OK;
 }
 
 cc_status cc_create(int32_t n, int64_t nnz, const int64_t* row_off, const int32_t* col, int32_t k,

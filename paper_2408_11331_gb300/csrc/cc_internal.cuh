@@ -543,5 +543,11 @@ constexpr int kKernelsOutsideRegions = kKernelsPerSweep + kGatesPerSweep - (12 +
 cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaEvent_t prop0,
                          cudaEvent_t prop1, cudaStream_t body = nullptr);
 cudaError_t prepare_propose(int* blocks_per_sm);
+// The proposal step's scoring kernels alone (own-cluster sums, candidate
+// bids) on the current state, for timing; they write only aown, act (the
+// same values on the same state) and the bids, which launch_clear_bids
+// empties again.  Nothing else of the state changes.
+cudaError_t launch_propose_probe(const SweepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_clear_bids(const SweepArgs& a, int grid, cudaStream_t s);
 
 }  // namespace ccg

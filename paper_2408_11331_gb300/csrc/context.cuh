@@ -75,6 +75,7 @@ struct cc_ctx {
     long long* eoff = nullptr;
     long long* ccnt = nullptr;          // colouring scratch (2 (n + 2)) and a flag
     int ncls = 1;                       // colour classes (1 without colour_batched)
+    bool tuned = true;                  // autotune: lanes chosen (or not to be tuned)
     ccg::DevState* st = nullptr;
     cc_sweep_info* hist = nullptr;
     int hist_cap = 0;
@@ -155,7 +156,9 @@ int ctx_async_poll(cc_ctx* c, cc_status* st);
 int ctx_async_poll_step(cc_ctx* c, cc_status* st);
 cc_status ctx_async_continue(cc_ctx* c);
 
-// Whether a job of these sizes fits the place of job j (see ctx_load_job).
+// Whether a job of these sizes fits the place of job j (see ctx_load_job):
+// no more vertices, CSR entries, partitions, label rows or keys than the
+// place, and at least a quarter of its vertices and CSR entries.
 bool ctx_slot_fits(const cc_ctx* c, int j, const JobInput& in);
 
 // Loads a new job into the place of job j, whose run has ended and whose
@@ -164,9 +167,10 @@ bool ctx_slot_fits(const cc_ctx* c, int j, const JobInput& in);
 // j's ranges (vertices the new job does not use go to an idle job that
 // never runs; CSR entries it does not use become self-loops of its last
 // vertex, which the method ignores), job j's record restarts at the new
-// job's singleton start, and the next sweep rebuilds the contingency table
-// from C for all jobs.  The new job's results are then those of running it
-// alone.  Host inputs are read before the call returns.  The run goes on
+// job's singleton start, the finished job's contingency keys get count 0
+// and the new job's singleton keys are inserted (only if the table runs
+// short is it rebuilt from C, in the next sweep).  The new job's results are
+// then those of running it alone.  Host inputs are read before the call returns.  The run goes on
 // with ctx_async_continue.  Errors: CC_ERR_INVALID (malformed input; the
 // context is unchanged), CC_ERR_OOM, CC_ERR_CUDA.
 cc_status ctx_load_job(cc_ctx* c, int j, const JobInput& in);

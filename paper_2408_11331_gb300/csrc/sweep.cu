@@ -116,7 +116,7 @@ __global__ void k_begin(SweepArgs a)
     }
 }
 
-constexpr int kInflight = 4;  // loads per lane issued before the first is used
+constexpr int kInflight = 2;  // loads per lane issued before the first is used
 
 __device__ __forceinline__ int group_sum(int x, int gs)
 {
@@ -378,29 +378,46 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
         // singleton candidates fill the scratch from the front, the others
         // from the back, so that scoring rounds take one path each
         int ns = 0, nt = 0;
+        // the loads of all kChunks chunks first (entries, then clusters), so
+        // that their latencies overlap; then each chunk's votes and compaction
+        int vc[kChunks], uc[kChunks], xc[kChunks], cvc[kChunks], jc[kChunks];
+#pragma unroll
         for (int c = 0; c < kChunks; ++c) {
             const long long ep = base + c * 32 + lane;
-            long long e = ep;
-            int v = 0, u = 0, x = -1, j = 0, cv = 0;
+            vc[c] = 0;
+            uc[c] = 0;
+            jc[c] = 0;
             if (ep < count) {
-                if (a.colour_mode) e = __ldg(a.eidx + ebase + ep);
-                v = __ldg(a.src + e);
-                if (!kSingle) j = __ldg(a.jid + v);
+                const long long e = a.colour_mode ? (long long)__ldg(a.eidx + ebase + ep) : ep;
+                vc[c] = __ldg(a.src + e);
+                uc[c] = __ldg(a.col + e);
+                if (!kSingle) jc[c] = __ldg(a.jid + vc[c]);
             }
+        }
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c) {
+            const long long ep = base + c * 32 + lane;
+            xc[c] = -1;
+            cvc[c] = 0;
+            if (ep < count && uc[c] != vc[c] && (kSingle || !a.js[jc[c]].stop)) {
+                xc[c] = __ldg(a.C + uc[c]);
+                cvc[c] = __ldg(a.C + vc[c]);
+            }
+        }
+        for (int c = 0; c < kChunks; ++c) {
+            const long long ep = base + c * 32 + lane;
+            const int v = vc[c], u = uc[c], j = jc[c];
+            int x = xc[c];
+            const int cv = cvc[c];
             // entries of stopped jobs are not scored; a chunk of only such
             // entries is skipped whole
             const bool live = ep < count && (kSingle || !a.js[j].stop);
             if (__all_sync(kFull, !live)) continue;
-            if (live) {
-                u = __ldg(a.col + e);
-                if (u != v) {
-                    x = __ldg(a.C + u);
-                    cv = __ldg(a.C + v);
-                    if (x == cv) x = -1;
-                    // active set: only candidates that changed, unless v is
-                    // scored in full
-                    else if (a.active_set && !all && !a.act[v] && a.chg[x] != last) x = -1;
-                }
+            if (live && x >= 0) {
+                if (x == cv) x = -1;
+                // active set: only candidates that changed, unless v is
+                // scored in full
+                else if (a.active_set && !all && !a.act[v] && a.chg[x] != last) x = -1;
             }
             const unsigned long long pair = x >= 0 ? ((unsigned long long)(unsigned)v << 32) | (unsigned)x : kEmpty;
             const unsigned same = __match_any_sync(kFull, pair);
@@ -431,31 +448,48 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
             nt += __popc(kt);
         }
         __syncwarp();
-        const int nf = ns + nt;
-        for (int r0 = 0; r0 < nf; r0 += per) {
+        // singleton candidates: two label rows compared, half the lanes per
+        // item of the cluster candidates (a plain streaming compare)
+        {
+            const int gr = gs > 1 ? gs >> 1 : 1, pr = 32 / gr, lr = lane & (gr - 1);
+            for (int r0 = 0; r0 < ns; r0 += pr) {
+                const int q = r0 + lane / gr;
+                const bool valid = q < ns;
+                const int ev = valid ? es.v[q] : 0, eu = valid ? es.u[q] : 0, ex_ = valid ? es.x[q] : 0;
+                const int sa = valid ? es.sa[q] : 0, Aa = valid ? es.Aa[q] : 0;
+                const JobInfo J = kSingle ? J0 : a.job[valid ? es.j[q] : 0];
+                int part = 0;
+                if (valid) part = row_part(a.G + row_of(J, eu), a.G + row_of(J, ev), J.kp >> 2, lr, gr);
+                part = group_sum(part, gr);
+                if (valid && lr == 0) {
+                    const int k = J.k, A = part - (J.kp - k);
+                    const int dD = 2 * (Aa - k - A) - k * (sa - 1 - 1);
+                    if (dD < 0) atomicMin(&a.best[ev], pack_key(dD, ex_));
+                }
+            }
+        }
+        // other clusters: summary rows, then probes where the bound leaves
+        // the move open
+        for (int r0 = 0; r0 < nt; r0 += per) {
             const int qq = r0 + lane / gs;
-            const bool valid = qq < nf;
-            const int q = qq < ns ? qq : (int)span - 1 - (qq - ns);
-            const int ev = valid ? es.v[q] : 0, eu = valid ? es.u[q] : 0, ex_ = valid ? es.x[q] : 0;
+            const bool valid = qq < nt;
+            const int q = (int)span - 1 - qq;
+            const int ev = valid ? es.v[q] : 0, ex_ = valid ? es.x[q] : 0;
             const int sx = valid ? es.sx[q] : 0, sa = valid ? es.sa[q] : 0, Aa = valid ? es.Aa[q] : 0;
             const JobInfo J = kSingle ? J0 : a.job[valid ? es.j[q] : 0];
             const int k = J.k;
-            const bool single = valid && sx == 1;
-            const bool table = valid && sx > 1;
             const int* gv = a.G + row_of(J, valid ? ev : J.vo);
-            // part = matching labels with u's row (a singleton) or the exact
-            // summary part (another cluster); ub only for the latter
+            // part = the exact summary part, ub its upper bound
             int part = 0, ub = 0;
-            if (single) part = row_part(a.G + row_of(J, eu), gv, J.kp >> 2, l, gs);
-            if (table) summary_part(a, J, gv, ex_, sx, l, gs, part, ub);
+            if (valid) summary_part(a, J, gv, ex_, sx, l, gs, part, ub);
             part = group_sum(part, gs);
             ub = group_sum(ub, gs);
-            const bool open = table && 2 * (Aa - k - ub) - k * (sa - 1 - sx) < 0;
+            const bool open = valid && 2 * (Aa - k - ub) - k * (sa - 1 - sx) < 0;
             int pb = 0;
             if (open) pb = probe_part(a, J, a.table, mask, gv, ex_, sx, l, gs);
             pb = group_sum(pb, gs);
-            if ((single || open) && l == 0) {
-                const int A = single ? part - (J.kp - k) : part + pb;
+            if (open && l == 0) {
+                const int A = part + pb;
                 const int dD = 2 * (Aa - k - A) - k * (sa - 1 - sx);
                 if (dD < 0) atomicMin(&a.best[ev], pack_key(dD, ex_));
             }
@@ -1146,6 +1180,30 @@ inline int jobs_grid(int jobs)
 int lanes_for_k(int k)
 {
     return lanes_per_item(k);
+}
+
+__global__ void k_clear_bids(SweepArgs a)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) a.best[v] = kEmpty;
+}
+
+cudaError_t launch_propose_probe(const SweepArgs& a, int grid, cudaStream_t s)
+{
+    if (a.jobs == 1) {
+        k_own<true><<<grid, kBlock, 0, s>>>(a);
+        k_edges<true><<<grid, kBlock, 0, s>>>(a);
+    } else {
+        k_own<false><<<grid, kBlock, 0, s>>>(a);
+        k_edges<false><<<grid, kBlock, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_bids(const SweepArgs& a, int grid, cudaStream_t s)
+{
+    k_clear_bids<<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t prepare_propose(int* blocks_per_sm)

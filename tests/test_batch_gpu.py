@@ -285,3 +285,18 @@ def test_batch_colour_batched(cc):
             r = oracle.colour_run(ro, col, lab, 20)
             assert b.history(j) == r.stats
             np.testing.assert_array_equal(ids[b.offsets[j]:b.offsets[j + 1]], r.C)
+
+
+def test_batch_autotune(cc):
+    """Autotuned lanes in a batch: every job equals the oracle's run alone."""
+    jobs = _mixed_jobs(6, 535)
+    o = cc.cc_default_options()
+    o.autotune = 1
+    o.active_set = 1
+    with cc.ConsensusBatch(jobs, o) as b:
+        b.run_until_converged(20)
+        ids = b.cluster_ids()
+        for j, (ro, col, lab) in enumerate(jobs):
+            r = oracle.sync_run(ro, col, lab, 20)
+            assert b.history(j) == r.stats
+            np.testing.assert_array_equal(ids[b.offsets[j]:b.offsets[j + 1]], r.C)

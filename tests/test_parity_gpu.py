@@ -599,3 +599,29 @@ def test_colour_batched_stepwise_and_warm_start(cc):
         ref2 = oracle.colour_run(ro, col, lab, 20)
         assert job.run_until_converged(20) == ref2.sweeps
         assert job.history() == ref2.stats
+
+
+# ------------------------------------------------------------- autotune
+
+
+def test_autotune_same_results_and_record(cc):
+    """cc_options.autotune: the first run times the candidate lane counts on
+    the state after its first sweep and keeps the fastest; the run equals the
+    oracle's, the choice is recorded for the lane bin, and a second context of
+    that bin reuses it with identical results."""
+    from paper_2408_11331_gb300 import _native
+    import ctypes
+
+    c = make_config("lfr", n=20000, k=37, cmin=20, cmax=1000, max_deg=1000, seed=17)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    ref = oracle.sync_run(ro, col, lab, 20)
+    assert_same(gpu_run(cc, ro, col, lab, 20, autotune=1), ref)
+    rec = (ctypes.c_int32 * 6)()
+    _native._check(_native.lib.cc_autotune_record(6, rec), None)
+    assert rec[2] in (2, 4, 8)  # k = 37 is in the bin of 21..40 partitions (4 lanes automatic)
+    with cc.Consensus(ro, col, lab, options(cc, autotune=1)) as job:
+        for _ in range(2):
+            job.reset()
+            assert job.run_until_converged(20) == ref.sweeps
+            assert job.history() == ref.stats
+            np.testing.assert_array_equal(job.cluster_ids(), ref.C)
