@@ -1033,10 +1033,14 @@ __global__ void k_load_keys(SweepArgs a, JobInfo J, long long vo)
     if (used) atomicAdd(&st->used, (unsigned long long)used);
 }
 
-__global__ void k_load_check_fill(DevState* st)
+// Before the new job's keys go in: if they could take the table past 7/8
+// of its slots (the finished job's keys still hold theirs), they are not
+// inserted and the next sweep rebuilds the table from C instead, so that
+// probing never runs in a nearly full table.
+__global__ void k_load_check_fill(DevState* st, unsigned long long new_keys)
 {
     const unsigned long long cap = st->mask + 1;
-    if (st->used > cap - (cap >> 3)) st->tvalid = 0;  // past 7/8: rebuild in the next sweep
+    if (st->used + new_keys > cap - (cap >> 3)) st->tvalid = 0;
 }
 
 // Singleton state of the place's vertices (stamped as changed in the sweep
@@ -1368,8 +1372,8 @@ cc_status ctx_load_job(cc_ctx* c, int j, const JobInput& in)
     // table rebuild in the next sweep
     if (e == cudaSuccess) {
         k_load_state<<<g, 256, 0, c->stream>>>(c->args, J.vo, ncap, J.go, n * J.kp);
+        k_load_check_fill<<<1, 1, 0, c->stream>>>(c->st, (unsigned long long)keys);
         k_load_keys<<<g, 256, 0, c->stream>>>(c->args, J, J.vo);
-        k_load_check_fill<<<1, 1, 0, c->stream>>>(c->st);
         e = cudaGetLastError();
     }
     JobState jsr;

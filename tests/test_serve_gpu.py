@@ -242,3 +242,25 @@ def test_serve_loads_a_waiting_job_into_a_running_context(cc):
             r = srv.result(t)
             assert r["status"] == 0 and r["sweeps"] == ref.sweeps and r["F"] == ref.F, (t, r["F"], ref.F)
             np.testing.assert_array_equal(r["labels"], oracle.renumber(ref.C))
+
+
+@pytest.mark.timeout(300)
+def test_serve_many_loads_into_one_context(cc):
+    """Forty jobs of similar size through one context of eight places: most
+    jobs are loaded into the place of a finished one (the table keeps the
+    other jobs' counts, or is rebuilt when it would run short), and every job
+    equals the oracle's run of it alone."""
+    rng = np.random.default_rng(77)
+    jobs = []
+    for j in range(40):
+        d = make_job(np.random.default_rng(int(rng.integers(0, 2 ** 62))), int(rng.integers(1200, 1600)),
+                     "lfr" if j % 2 else "sbm", int(rng.integers(8, 11)))
+        jobs.append((d["row_off"], d["col"], d["labels"]))
+    refs = _refs(jobs)
+    with cc.Server(max_active=1, max_batch_jobs=8) as srv:
+        tickets = [srv.submit(*j) for j in jobs]
+        srv.drain()
+        st = srv.stats()
+        assert st["completed"] == 40 and st["failed"] == 0
+        assert st["admitted_running"] >= 10, st
+        _check(srv, tickets, jobs, refs)
