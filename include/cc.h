@@ -294,6 +294,9 @@ cc_status cc_sweep(cc_ctx* ctx, cc_sweep_info* info);
  * Sweeps are submitted as CUDA graphs of up to 4 unrolled sweeps (a sweep is
  * skipped on the device once the run has stopped); the host reads the stop
  * flag after each graph, so a run costs one synchronisation per 4 sweeps.
+ * A context of several jobs (cc_batch_create; unless no_regions is set) runs
+ * instead as one graph launch: a conditional loop repeats the sweep until
+ * the run stops, and the host synchronises once.
  * *sweeps_done (may be NULL) counts every sweep run, the final empty one
  * included.  Errors as cc_sweep. */
 cc_status cc_run_until_converged(cc_ctx* ctx, int32_t max_sweeps, int32_t* sweeps_done);
@@ -302,7 +305,9 @@ cc_status cc_run_until_converged(cc_ctx* ctx, int32_t max_sweeps, int32_t* sweep
  * call, from CUDA events recorded inside its graphs on the context's stream:
  * sweep_ms[s] covers sweep s (all its kernels), propose_ms[s] its proposal
  * kernels (k_own, k_edges, k_collect); with colour_batched, entry s covers
- * the s-th colour class run (a sweep is one run of every class).  At most max entries are written to
+ * the s-th colour class run (a sweep is one run of every class).  A run that
+ * was one graph launch (a context of several jobs) has one entry for it, with
+ * propose_ms 0 (the proposal kernels are not timed apart inside the loop).  At most max entries are written to
  * each non-NULL array; *count receives the number of sweeps timed.  A sweep
  * abandoned for lack of table space and retried is timed once per attempt. */
 cc_status cc_last_run_timing(cc_ctx* ctx, int32_t max, float* sweep_ms, float* propose_ms, int32_t* count);

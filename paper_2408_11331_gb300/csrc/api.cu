@@ -85,6 +85,8 @@ void free_all(cc_ctx* c)
     c->own_stream = nullptr;
     if (c->body_stream) cudaStreamDestroy(c->body_stream);
     c->body_stream = nullptr;
+    if (c->loop_stream) cudaStreamDestroy(c->loop_stream);
+    c->loop_stream = nullptr;
 }
 
 unsigned long long next_pow2(unsigned long long x)
@@ -239,6 +241,54 @@ cc_status ensure_graph(cc_ctx* c, int limit, RunGraph** out)
     return CC_OK;
 }
 
+// A whole run of a multi-job context as one graph launch: a WHILE node
+// repeats the sweep body until the run stops (at most `limit` sweeps' bodies
+// plus 64 for abandoned and retried ones).  Returns the CUDA error instead of
+// failing the context, so that the caller can fall back to chunks.
+cudaError_t ensure_loop_graph(cc_ctx* c, int limit, RunGraph** out)
+{
+    auto it = c->graphs.find(-limit);
+    if (it != c->graphs.end()) {
+        *out = &it->second;
+        return cudaSuccess;
+    }
+    RunGraph g;
+    g.bound.resize(2);
+    cudaError_t e = cudaSuccess;
+    for (auto& ev : g.bound)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(c->own_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = cudaEventRecordWithFlags(g.bound[0], c->own_stream, cudaEventRecordExternal);
+        const int budget = (int)std::min<long long>((long long)limit * c->ncls + 64, 1LL << 30);
+        if (e == cudaSuccess)
+            e = capture_run_loop(c->args, c->rows, c->grid, c->own_stream, c->loop_stream, c->body_stream, budget);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(g.bound[1], c->own_stream, cudaEventRecordExternal);
+        for (cudaStream_t st : {c->body_stream, c->loop_stream}) {
+            cudaStreamCaptureStatus bs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(st, &bs) == cudaSuccess && bs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t left = nullptr;
+                cudaStreamEndCapture(st, &left);  // a capture left open by a failure
+                if (left) cudaGraphDestroy(left);
+            }
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(c->own_stream, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        destroy_graph(g);
+        cudaGetLastError();  // the failure is reported to the caller, not left pending
+        return e;
+    }
+    auto ins = c->graphs.emplace(-limit, g);
+    *out = &ins.first->second;
+    return cudaSuccess;
+}
+
 // Sweep bodies per graph launch: a run launches the graph until the device
 // says the run has stopped, so at most kChunk - 1 skipped sweep bodies are
 // submitted after the last sweep.  With colour_batched a body runs one colour
@@ -314,6 +364,7 @@ cc_status tune_lanes(cc_ctx* c)
 // Runs every job until it stops; *done = largest number of sweeps of a job in this run.
 cc_status run(cc_ctx* c, int limit, int* done)
 {
+    const int full_limit = limit;
     CC_CUDA(c, launch_run_begin(c->args, limit, c->stream));
     c->launches += 1;
     c->sweep_ms.clear();
@@ -346,10 +397,28 @@ cc_status run(cc_ctx* c, int limit, int* done)
         c->tuned = true;
         limit -= st.run_bodies > 0 ? 1 : 0;
     }
+    // a multi-job context (unless profiling without regions) runs the rest as
+    // one graph launch
+    RunGraph* lg = nullptr;
+    const bool loop = c->jobs > 1 && !c->opt.no_regions && c->loop_ok && !(before > 0 && (st.stop || st.err));
+    if (loop && ensure_loop_graph(c, full_limit, &lg) != cudaSuccess) c->loop_ok = false;
+    if (loop && c->loop_ok) {
+        CC_CUDA(c, cudaGraphLaunch(lg->exec, c->stream));
+        r = read_state(c, &st);
+        if (r != CC_OK) return r;
+        c->launches += (long long)(st.run_bodies - before) * (kKernelsOutsideRegions + 1);
+        float x = 0.f;
+        CC_CUDA(c, cudaEventElapsedTime(&x, lg->bound[0], lg->bound[1]));
+        c->sweep_ms.push_back(x);
+        c->propose_ms.push_back(0.f);
+        before = st.run_bodies;
+    }
     const int chunk = chunk_bodies(c, std::max(limit, 1));
     RunGraph* g = nullptr;
-    r = ensure_graph(c, chunk, &g);
-    if (r != CC_OK) return r;
+    if (!(before > 0 && (st.stop || st.err))) {
+        r = ensure_graph(c, chunk, &g);
+        if (r != CC_OK) return r;
+    }
     // a sweep abandoned for lack of table space is retried in the next body,
     // so the number of launches is bounded by the limit plus the retries
     const long long budget = launch_budget(c, std::max(limit, 1), chunk);
@@ -547,6 +616,7 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     CC_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     CC_TRY(cudaStreamCreateWithPriority(&c->own_stream, cudaStreamNonBlocking, priority));
     CC_TRY(cudaStreamCreateWithPriority(&c->body_stream, cudaStreamNonBlocking, priority));
+    CC_TRY(cudaStreamCreateWithPriority(&c->loop_stream, cudaStreamNonBlocking, priority));
     // pooled memory is allocated in the order of the context's own stream, so
     // such a context runs on that stream
     c->stream = (stream && !pool) ? static_cast<cudaStream_t>(stream) : c->own_stream;

@@ -543,6 +543,12 @@ constexpr int kKernelsOutsideRegions = kKernelsPerSweep + kGatesPerSweep - (12 +
 cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaEvent_t prop0,
                          cudaEvent_t prop1, cudaStream_t body = nullptr);
 cudaError_t prepare_propose(int* blocks_per_sm);
+// Adds to the graph being captured on s a WHILE node whose body (captured on
+// `loop`, with the sweep's regions on `body`) is one sweep followed by a gate
+// that repeats it until the run stops, fails or has run `budget` bodies: a
+// whole run as one graph launch.
+cudaError_t capture_run_loop(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaStream_t loop,
+                             cudaStream_t body, int budget);
 // The proposal step's scoring kernels alone (own-cluster sums, candidate
 // bids) on the current state, for timing; they write only aown, act (the
 // same values on the same state) and the bids, which launch_clear_bids

@@ -24,6 +24,8 @@ struct cc_ctx {
     cudaStream_t stream = nullptr;      // stream used by calls
     cudaStream_t own_stream = nullptr;  // stream created by the context (also used for capture)
     cudaStream_t body_stream = nullptr; // captures the bodies of a sweep graph's conditional regions
+    cudaStream_t loop_stream = nullptr; // captures the body of a run loop (batches: a run is one launch)
+    bool loop_ok = true;                // the run loop graph could be built (else: chunks of sweeps)
     cudaMemPool_t pool = nullptr;       // device memory comes from this pool (stream-ordered) if set
     std::vector<ccg::JobInfo> job;      // host copy of the job table
     std::vector<long long> F0;          // objective of each job at the singleton start
@@ -80,7 +82,7 @@ struct cc_ctx {
     cc_sweep_info* hist = nullptr;
     int hist_cap = 0;
     ccg::SweepArgs args{};
-    std::map<int, RunGraph> graphs;
+    std::map<int, RunGraph> graphs;     // key > 0: chunk of that many bodies; key < 0: run loop of that limit
     std::vector<float> sweep_ms;        // device time of each sweep of the last run
     std::vector<float> propose_ms;      // ... and of its proposal kernels
     long long launches = 0;             // kernels launched so far

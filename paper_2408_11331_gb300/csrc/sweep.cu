@@ -1169,6 +1169,14 @@ cudaError_t close_region(cudaStream_t b)
     return cudaStreamEndCapture(b, &g);
 }
 
+// End of one body of a run loop: go on while the run has not stopped, has no
+// error and has run fewer than `budget` sweep bodies.
+__global__ void k_loop_gate(cudaGraphConditionalHandle h, DevState* st, int budget)
+{
+    const bool more = !st->stop && !st->err && st->run_bodies < budget;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 inline int jobs_grid(int jobs)
 {
     int g = (jobs + 255) / 256;
@@ -1213,6 +1221,45 @@ cudaError_t prepare_propose(int* blocks_per_sm)
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&multi, k_edges<false>, kBlock, 0);
     *blocks_per_sm = single < multi ? single : multi;
     return e;
+}
+
+cudaError_t capture_run_loop(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaStream_t loop,
+                             cudaStream_t body, int budget)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureUnsupported;
+    // the loop is entered once per launch (default value 1); each body's gate
+    // decides whether another follows
+    cudaGraphConditionalHandle h = 0;
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, deps, edges, nd, &p);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCaptureToGraph(loop, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    e = launch_sweep(a, rows, grid, loop, nullptr, nullptr, body);
+    if (e == cudaSuccess) {
+        k_loop_gate<<<1, 1, 0, loop>>>(h, a.st, budget);
+        e = cudaGetLastError();
+    }
+    cudaGraph_t lg = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(loop, &lg);
+    return e != cudaSuccess ? e : e2;
 }
 
 cudaError_t launch_run_begin(const SweepArgs& a, int limit, cudaStream_t s)

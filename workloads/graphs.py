@@ -98,6 +98,22 @@ def _power_law_mean(expo, lo, hi):
 
 def lfr_like(n: int, avg_deg: float, max_deg: int, gamma: float, beta: float,
              cmin: int, cmax: int, mu: float, rng):
+    """LFR-style graph whose realised mean degree is ``avg_deg``: dropping
+    repeated pairs, self-loops and external pairs inside one community loses
+    a few percent of the stubs, so the graph is drawn once, its realised mean
+    degree measured, and drawn again from the same generator state with the
+    target raised by the lost share (see ``_lfr_draw`` for the model)."""
+    state = rng.bit_generator.state
+    row_off, col, truth = _lfr_draw(n, avg_deg, max_deg, gamma, beta, cmin, cmax, mu, rng)
+    got = len(col) / max(n, 1)
+    if got <= 0 or got >= avg_deg:
+        return row_off, col, truth
+    rng.bit_generator.state = state
+    return _lfr_draw(n, min(avg_deg * avg_deg / got, 0.9 * max_deg), max_deg, gamma, beta, cmin, cmax, mu, rng)
+
+
+def _lfr_draw(n: int, avg_deg: float, max_deg: int, gamma: float, beta: float,
+              cmin: int, cmax: int, mu: float, rng):
     """LFR-style benchmark graph built with a configuration model.
 
     Degrees follow a power law with exponent ``gamma`` on [d_min, max_deg],
