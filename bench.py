@@ -62,10 +62,8 @@ UNIT = "edge-partitions/s"
 # case of the same workload, scaled by nnz to the full size; reported as
 # roofline.traffic while the kernels are the ones captured (empty when they
 # changed since).
-PROPOSAL_TRAFFIC = {"knn_n2000000_k50": 62.89e9}
-PROPOSAL_TRAFFIC_SOURCE = {
-    "knn_n2000000_k50": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_own, k_edges, k_collect over one "
-                        "run at n=500000 (15.37 GB), scaled by nnz (x4.0921)"}
+PROPOSAL_TRAFFIC = {}
+PROPOSAL_TRAFFIC_SOURCE = {}
 
 
 def parse():

@@ -346,11 +346,13 @@ struct EdgeScratch {
 // is a candidate whose gain is >= 0 even with A_x at its bound k |x|); the
 // entries kept from kChunks chunks are then scored by groups of lanes.  A
 // singleton {u} is scored from the two label rows; another cluster from its
-// summary rows, then (unless the lower bound on dD from the summary is
-// already >= 0, in which case the move can never be proposed) from probes of
-// the open partitions.  A move with dD < 0 bids its packed (dD, C[u]) at
-// best[v] with an atomic minimum (a candidate kept in two chunks bids the
-// same key twice).  All group reductions are outside the branches, so every
+// summary rows, then from probes of the open partitions, unless the lower
+// bound on dD from the summary already rules the move out: a bound >= 0 (the
+// move is never proposed), or a packed (bound, C[u]) not below v's least bid
+// so far (bids only decrease, so the move cannot be v's least).  A move with
+// dD < 0 bids its packed (dD, C[u]) at best[v] with an atomic minimum (a
+// candidate kept in two chunks bids the same key twice).  The bids, and so
+// the proposals, do not depend on which candidates the bound skipped.  All group reductions are outside the branches, so every
 // lane of the warp takes part in every shuffle.
 template <bool kSingle>
 __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
@@ -479,12 +481,18 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
             const JobInfo J = kSingle ? J0 : a.job[valid ? es.j[q] : 0];
             const int k = J.k;
             const int* gv = a.G + row_of(J, valid ? ev : J.vo);
+            // v's least bid so far (read from L2, where the bids land); it
+            // only decreases, so an early read is a valid threshold
+            const unsigned long long cur = valid ? __ldcg(a.best + ev) : 0ull;
             // part = the exact summary part, ub its upper bound
             int part = 0, ub = 0;
             if (valid) summary_part(a, J, gv, ex_, sx, l, gs, part, ub);
             part = group_sum(part, gs);
             ub = group_sum(ub, gs);
-            const bool open = valid && 2 * (Aa - k - ub) - k * (sa - 1 - sx) < 0;
+            // the least dD the probes can give; open only if that could
+            // still be v's least bid
+            const int lb = 2 * (Aa - k - ub) - k * (sa - 1 - sx);
+            const bool open = valid && lb < 0 && pack_key(lb, ex_) < cur;
             int pb = 0;
             if (open) pb = probe_part(a, J, a.table, mask, gv, ex_, sx, l, gs);
             pb = group_sum(pb, gs);
