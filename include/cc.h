@@ -119,6 +119,14 @@ typedef struct {
                                device and lane bin (see cc_plan_batches) for the later contexts
                                of the process, which then skip the timing.  Results are
                                identical; only speed changes.  0 (default): automatic rule */
+    int32_t tight_rebuild;  /* Capacity of the rebuild of a heavy sweep (results are identical
+                               for every value).  0 (default): first a tight capacity, from
+                               the occupied slots at the sweep start at load <= 1/2 with room
+                               for a following light sweep; a build that does not fit it (an
+                               insert past 256 probes, load above 1/2, or too little room) is
+                               dropped and redone at the capacity that holds every key the
+                               sweep can create.  1: always that safe capacity.  2: the tight
+                               attempt is always dropped (for tests of the second attempt) */
 } cc_options;
 
 /* State of the contingency hash of a context. */

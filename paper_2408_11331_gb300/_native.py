@@ -40,7 +40,8 @@ class cc_options(ctypes.Structure):
                 ("table_log2", ctypes.c_int32), ("table_start_log2", ctypes.c_int32),
                 ("sweep_mode", ctypes.c_int32), ("lanes", ctypes.c_int32), ("active_set", ctypes.c_int32),
                 ("no_regions", ctypes.c_int32), ("empty_moves", ctypes.c_int32),
-                ("colour_batched", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("colour_batched", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("tight_rebuild", ctypes.c_int32)]
 
 
 class cc_table_info(ctypes.Structure):

@@ -530,6 +530,7 @@ cc_status check_options(const cc_options& opt, std::string* msg)
         return bad(CC_ERR_INVALID, "colour_batched must be 0 or 1");
     if (opt.colour_batched && opt.active_set) return bad(CC_ERR_INVALID, "colour_batched needs active_set = 0");
     if (opt.autotune != 0 && opt.autotune != 1) return bad(CC_ERR_INVALID, "autotune must be 0 or 1");
+    if (opt.tight_rebuild < 0 || opt.tight_rebuild > 2) return bad(CC_ERR_INVALID, "tight_rebuild must be 0, 1 or 2");
     return CC_OK;
 }
 
@@ -856,6 +857,7 @@ cc_status create_common(int jobs, const JobInput* in, bool on_device, const cc_o
     }
     a.active_set = c->opt.active_set;
     a.empty_moves = c->opt.empty_moves;
+    a.tight_mode = c->opt.tight_rebuild;
     a.chg = c->chg;
     a.prev = c->prev;
     a.act = c->act;

@@ -114,6 +114,10 @@ struct DevState {
     int all_active;              // 1: every vertex is scored in this sweep (first sweep of a run)
     int cls;                     // colour_batched: the class this sweep body runs
     int ncls;                    // colour_batched: number of classes (of the job with the most)
+    unsigned long long safe_mask;  // heavy sweep: capacity - 1 that holds every key it can create
+    int tight;                   // 1: the pending rebuild tries a capacity below safe_mask (checked)
+    int again;                   // 1: the tight attempt was too small; the rebuild runs again at safe_mask
+    int build_fail;              // 1: an insert of the tight attempt ran past its probe limit
 };
 
 // Arguments of the kernels (passed by value).
@@ -143,6 +147,7 @@ struct SweepArgs {
     int gs;                      // lanes that score one item (a power of two, 1..32)
     int active_set;              // 1: score only the active vertices (cc_options.active_set)
     int empty_moves;             // 1: a vertex may also move into a new cluster with its own id (cc_options.empty_moves)
+    int tight_mode;              // cc_options.tight_rebuild: 0 tight attempt first, 1 never, 2 always dropped
     int colour_mode;             // 1: colour-batched sweeps (cc_options.colour_batched): a sweep body
                                  //    runs the vertices of colour class st->cls only
     const int* vlist;            // colour_batched: vertices listed class by class (n)
@@ -387,19 +392,19 @@ __device__ __forceinline__ ulonglong2 entry_cas(int4* p, ulonglong2 cmp, ulonglo
 // slot either empty with count 0, or holding a key): a new key is written
 // together with its count by one 16-byte CAS; an existing key gets an atomic
 // add.  *inserted is set when this call created the slot.  Returns -1 if the
-// table is full.
+// key found no slot within `limit` probes (the whole table by default).
 // mark (0 or 1) goes into the new slot's staged-delta field: the rebuild
 // marks the keys whose summary entry is already final (see setup.cu) and
 // clears the mark again before any sweep stages deltas.
 __device__ __forceinline__ long long table_build_add(Slot* t, unsigned long long mask, unsigned long long key, int cnt,
-                                                     bool* inserted, int mark = 0)
+                                                     bool* inserted, int mark = 0, unsigned long long limit = ~0ull)
 {
     *inserted = false;
     const ulonglong2 empty = make_ulonglong2(kEmpty, 0ull);
     const ulonglong2 mine =
         make_ulonglong2(key, ((unsigned long long)(unsigned)mark << 32) | (unsigned long long)(unsigned)cnt);
     unsigned long long h = hash_key(key) & mask;
-    for (unsigned long long p = 0; p <= mask; ++p) {
+    for (unsigned long long p = 0; p <= mask && p < limit; ++p) {
         const ulonglong2 old = slot_cas(t + h, empty, mine);
         if (old.x == kEmpty && old.y == 0ull) {
             *inserted = true;
@@ -534,12 +539,17 @@ cudaError_t launch_run_begin(const SweepArgs& a, int limit, cudaStream_t s);
 // graph), the heavy path, its rollback, the light path and the end-of-sweep
 // rebuild become IF regions of the graph, each behind a one-thread gate
 // kernel, so a sweep launches only the regions it needs.
-constexpr int kKernelsPerRebuild = 8;
-constexpr int kKernelsPerSweep = 19 + 3 * kKernelsPerRebuild;  // kernels of a sweep without regions
-constexpr int kGatesPerSweep = 4;
+constexpr int kKernelsPerRebuild = 9;
+// regions: heavy path (mark, apply, rebuild), its second rebuild attempt,
+// heavy evaluation (eval, decide), rollback (undo, rebuild), light path
+// (stage, eval, decide), end-of-sweep rebuild
+constexpr int kKernelsInRegions = (2 + kKernelsPerRebuild) + kKernelsPerRebuild + 2 + (1 + kKernelsPerRebuild) + 3 +
+                                  kKernelsPerRebuild;
+constexpr int kKernelsPerSweep = 11 + kKernelsInRegions;  // kernels of a sweep without regions
+constexpr int kGatesPerSweep = 6;
 // kernels of a sweep graph outside its regions (gates included); the kernels
 // of the regions that run are counted on the device (DevState.region_launches)
-constexpr int kKernelsOutsideRegions = kKernelsPerSweep + kGatesPerSweep - (12 + 9 + 3 + kKernelsPerRebuild);
+constexpr int kKernelsOutsideRegions = kKernelsPerSweep + kGatesPerSweep - kKernelsInRegions;
 cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStream_t s, cudaEvent_t prop0,
                          cudaEvent_t prop1, cudaStream_t body = nullptr);
 cudaError_t prepare_propose(int* blocks_per_sm);

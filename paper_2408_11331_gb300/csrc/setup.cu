@@ -280,7 +280,13 @@ __device__ __forceinline__ bool rebuild_off(const DevState* st, int conditional)
 
 // Clears the slots of the capacity being built (st->new_mask + 1 of them),
 // the summary rows, the occupied-slot counter, and the staged size deltas
-// after an abandoned sweep.
+// after an abandoned sweep.  Summary rows: those of the live clusters (a warp
+// per 32 cluster ids, the lanes across each live row), which are the rows the
+// rebuild fills and the sweeps read.  The row of a dead cluster is never read
+// again, since no move enters an empty cluster, except with empty_moves (a
+// vertex may found a cluster under its own, possibly dead, id); then, and
+// when the table did not hold the counts of C before (a new start), every row
+// is cleared.
 __global__ void k_table_clear(SweepArgs a, long long rows, int conditional)
 {
     DevState* st = a.st;
@@ -290,7 +296,23 @@ __global__ void k_table_clear(SweepArgs a, long long rows, int conditional)
     const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (unsigned long long s = t0; s < cap; s += stride)
         reinterpret_cast<ulonglong2*>(a.table)[s] = make_ulonglong2(kEmpty, 0ull);
-    for (unsigned long long r = t0; r < (unsigned long long)rows; r += stride) a.summ[r] = make_int4(-1, 0, -1, 0);
+    const int4 none = make_int4(-1, 0, -1, 0);
+    if (a.empty_moves || !st->tvalid) {
+        for (unsigned long long r = t0; r < (unsigned long long)rows; r += stride) a.summ[r] = none;
+    } else {
+        const int lane = threadIdx.x & 31;
+        for (unsigned long long x0 = t0 - lane; x0 < (unsigned long long)a.n; x0 += stride) {
+            const unsigned long long x = x0 + lane;
+            unsigned live = __ballot_sync(0xffffffffu, x < (unsigned long long)a.n && a.size[x] > 0);
+            while (live) {
+                const long long xx = (long long)x0 + __ffs(live) - 1;
+                live &= live - 1;
+                const JobInfo& J = a.job[a.jid[xx]];
+                int4* row = a.summ + row_of(J, xx);
+                for (int q = lane; q < J.kp; q += 32) row[q] = none;
+            }
+        }
+    }
     if (st->abort)
         for (unsigned long long v = t0; v < (unsigned long long)a.n; v += stride) a.dsize[v] = 0;
     if (t0 == 0) st->used = 0;
@@ -395,6 +417,11 @@ __device__ __forceinline__ unsigned long long segment_max(unsigned long long x, 
 // id, as the table scan would rank them), adds its keys' -2 n^2 to the job's
 // F' in a heavy sweep (eval), and marks those keys so that the scan skips
 // them.  Keys of clusters spread over several warps are left to the scan.
+// A tight attempt (see k_build_check) gives every insert kTightProbes probes;
+// an insert that finds no slot within them flags the attempt as failed, and
+// the warps stop inserting.
+constexpr unsigned long long kTightProbes = 256;
+
 __global__ void k_table_build(SweepArgs a, int conditional, int eval)
 {
     extern __shared__ long long dyn_jobs[];
@@ -402,6 +429,8 @@ __global__ void k_table_build(SweepArgs a, int conditional, int eval)
     if (rebuild_off(st, conditional)) return;
     __shared__ unsigned long long s_used;
     if (threadIdx.x == 0) s_used = 0;
+    const bool tight = st->tight != 0;
+    const unsigned long long limit = tight ? kTightProbes : ~0ull;
     const bool ev = eval && st->heavy;
     JobAcc acc(ev ? job_smem_init(a.jobs, dyn_jobs) : nullptr, &a.js[0].recompute, kJobStride);
     __syncthreads();
@@ -410,6 +439,7 @@ __global__ void k_table_build(SweepArgs a, int conditional, int eval)
     const int lane = threadIdx.x & 31;
     unsigned long long used = 0;  // slots this warp created (lane 0 counts)
     for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+        if (tight && __any_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&st->build_fail) != 0)) break;
         const long long m = base + threadIdx.x;
         const long long wb = m - lane;  // first member of this warp's window
         const bool valid = m < a.n;
@@ -440,7 +470,10 @@ __global__ void k_table_build(SweepArgs a, int conditional, int eval)
             const bool leader = on && (__ffs(same) - 1) == lane;
             bool ins = false;
             if (leader) {
-                if (table_build_add(a.table, mask, key, cnt, &ins, whole ? 1 : 0) < 0) set_err(st, CC_ERR_TABLE_FULL);
+                if (table_build_add(a.table, mask, key, cnt, &ins, whole ? 1 : 0, limit) < 0) {
+                    if (tight) st->build_fail = 1;
+                    else set_err(st, CC_ERR_TABLE_FULL);
+                }
                 if (ev && whole) acc.add(job, -2LL * cnt * cnt);
             }
             used += __popc(__ballot_sync(0xffffffffu, ins));
@@ -479,7 +512,7 @@ __global__ void k_summ_top(SweepArgs a, int conditional, int eval)
 {
     extern __shared__ long long dyn_jobs[];
     DevState* st = a.st;
-    if (rebuild_off(st, conditional)) return;
+    if (rebuild_off(st, conditional) || st->again) return;
     const bool ev = eval && st->heavy;
     JobAcc acc(ev ? job_smem_init(a.jobs, dyn_jobs) : nullptr, &a.js[0].recompute, kJobStride);
     const unsigned long long cap = st->new_mask + 1;
@@ -516,9 +549,39 @@ __global__ void k_summ_top(SweepArgs a, int conditional, int eval)
     if (ev) job_acc_finish(acc, a.jobs);
 }
 
+// Check of a tight attempt, after its build: the table must have taken every
+// key within the probe limit, at load <= 1/2, with room left below the fill
+// limit for the new keys of a light sweep (at most 2 x sum_j k_j n_j / 8).
+// Otherwise the attempt is dropped (its part of F' is cleared; the summary
+// pass and the done step skip it) and the rebuild runs again at the capacity
+// that holds every key the sweep can create.  One block.
+__global__ void k_build_check(SweepArgs a, int conditional)
+{
+    DevState* st = a.st;
+    if (rebuild_off(st, conditional)) return;
+    __shared__ int fail;
+    if (threadIdx.x == 0) {
+        fail = 0;
+        if (st->tight) {
+            const unsigned long long cap = st->new_mask + 1, fill = cap - (cap >> 3);
+            const unsigned long long room = 2 * ((a.keys + 7) / 8);
+            fail = st->build_fail || st->used > cap / 2 || st->used + room > fill || a.tight_mode == 2;
+        }
+    }
+    __syncthreads();
+    if (fail)
+        for (int j = threadIdx.x; j < a.jobs; j += blockDim.x) a.js[j].recompute = 0;
+    if (threadIdx.x == 0) {
+        if (fail) st->new_mask = st->safe_mask;
+        st->again = fail;
+        st->tight = 0;
+        st->build_fail = 0;
+    }
+}
+
 __global__ void k_table_done(DevState* st, int conditional)
 {
-    if (rebuild_off(st, conditional)) return;
+    if (rebuild_off(st, conditional) || st->again) return;
     st->live = (long long)st->used;
     st->mask = st->new_mask;
     st->rebuild = 0;
@@ -773,6 +836,7 @@ cudaError_t launch_table_rebuild(const SweepArgs& a, long long rows, bool condit
     k_scan_write<<<nb, 1024, 0, s>>>(a, c);
     k_members_scatter<<<grid_for(a.n), kSetupBlock, 0, s>>>(a, c);
     k_table_build<<<grid_for(a.n), kSetupBlock, eval ? smem_jobs_bytes(a.jobs) : 0, s>>>(a, c, eval ? 1 : 0);
+    k_build_check<<<1, 256, 0, s>>>(a, c);
     k_summ_top<<<grid_for((long long)a.mask_max + 1), kSetupBlock, eval ? smem_jobs_bytes(a.jobs) : 0, s>>>(a, c,
                                                                                                  eval ? 1 : 0);
     k_table_done<<<1, 1, 0, s>>>(a.st, c);

@@ -10,7 +10,9 @@
 //                distinct candidates of every 128 CSR entries and bidding,
 //                then the proposal list
 //   route        heavy or light evaluation of the kept moves P1 (results agree)
-//   [heavy path] apply P1, rebuild the table, F' - F per job; commit, or
+//   [heavy path] apply P1, rebuild the table (first at a tight capacity, and
+//                again at a safe one if the keys did not fit), F' - F per
+//                job; commit, or
 //   [rollback]   undo and rebuild
 //   [light path] singleton guard; stage size and count deltas; exact dF per job
 //   bid          matching jobs: drop staged deltas, bid (dD, v) at both clusters
@@ -102,6 +104,9 @@ __global__ void k_begin(SweepArgs a)
         st->heavy = 0;
         st->rollback = 0;
         st->active = 0;
+        st->tight = 0;
+        st->again = 0;
+        st->build_fail = 0;
     }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.jobs; j += gridDim.x * blockDim.x) {
         JobState& s = a.js[j];
@@ -593,7 +598,19 @@ __global__ void k_route(SweepArgs a)
     if (bound > total_keys) bound = total_keys;
     unsigned long long c = a.cap_min;
     while (c < 2 * bound && c < a.mask_max + 1) c <<= 1;
-    st->new_mask = c - 1;
+    // First a tight capacity: the occupied slots of the sweep start (the
+    // moves of a heavy sweep mostly merge keys) at load <= 1/2, with room
+    // below the fill limit for the new keys of a following light sweep
+    // (2 x sum k n / 8 at most).  The rebuild checks that the keys fit
+    // (k_build_check) and otherwise builds again at c.
+    const unsigned long long est = st->tvalid ? st->used : total_keys;
+    const unsigned long long room = 2 * ((total_keys + 7) / 8);
+    unsigned long long t = a.cap_min;
+    while ((t < 2 * est || t - (t >> 3) < est + room) && t < c) t <<= 1;
+    st->safe_mask = c - 1;
+    st->tight = (t < c && a.tight_mode != 1) ? 1 : 0;
+    if (!st->tight) t = c;
+    st->new_mask = t - 1;
     st->rebuild = 1;
 }
 
@@ -678,11 +695,15 @@ __global__ void k_h_decide(SweepArgs a)
             s.mode = s.nprop > 0 ? 2 : 0;
             s.dF = 0;
             s.moves = 0;
-            if (s.np1 > 0) {
-                s.rollback = 1;
+            if (s.np1 > 0) s.rollback = 1;
+            // the rollback rebuilds at the capacity that holds every key the
+            // sweep can create, so that the matching fallback's inserts fit;
+            // a job that falls back without moves to undo also needs that
+            // room when the heavy rebuild was a tight one
+            if (s.np1 > 0 || (s.mode == 2 && st->mask != st->safe_mask)) {
                 st->rollback = 1;
                 st->rebuild = 1;
-                st->new_mask = st->mask;
+                st->new_mask = st->safe_mask;
             }
         }
     }
@@ -1123,13 +1144,14 @@ __global__ void k_end(SweepArgs a)
 // an IF node whose condition a one-thread gate kernel sets from the control
 // block, so a sweep that does not need a region skips its launches instead of
 // running kernels that return at once.
-enum Gate { kGateHeavy = 0, kGateRollback = 1, kGateLight = 2, kGateRebuild = 3 };
+enum Gate { kGateHeavy = 0, kGateRollback = 1, kGateLight = 2, kGateRebuild = 3, kGateRetry = 4, kGateHeavyEval = 5 };
 
 __global__ void k_gate(cudaGraphConditionalHandle h, DevState* st, int which, int kernels)
 {
     const bool run = !st->skip && !st->err;
     bool on = false;
-    if (which == kGateHeavy) on = run && st->heavy;
+    if (which == kGateHeavy || which == kGateHeavyEval) on = run && st->heavy;
+    else if (which == kGateRetry) on = run && st->heavy && st->rebuild;
     else if (which == kGateRollback) on = run && st->heavy && st->rollback;
     else if (which == kGateLight) on = run && !st->heavy && st->nprop > 0;
     else on = st->rebuild && !st->err;
@@ -1312,14 +1334,31 @@ cudaError_t launch_sweep(const SweepArgs& a, long long rows, int grid, cudaStrea
     }
     k_route<<<1, 1, 0, s>>>(a);
     {
-        cudaStream_t r = open(kGateHeavy, 4 + kKernelsPerRebuild);
+        cudaStream_t r = open(kGateHeavy, 2 + kKernelsPerRebuild);
         if (e != cudaSuccess) return e;
         k_h_mark<<<g2, kBlock, js1, r>>>(a);
         k_h_apply<<<g2, kBlock, 0, r>>>(a, 0);
         e = launch_table_rebuild(a, rows, true, r, true);
         if (e != cudaSuccess) return e;
+        close();
+        if (e != cudaSuccess) return e;
+    }
+    {
+        // second attempt of the heavy rebuild, when the tight capacity was
+        // too small (the rebuild is still pending)
+        cudaStream_t r = open(kGateRetry, kKernelsPerRebuild);
+        if (e != cudaSuccess) return e;
+        e = launch_table_rebuild(a, rows, true, r, true);
+        if (e != cudaSuccess) return e;
+        close();
+        if (e != cudaSuccess) return e;
+    }
+    {
+        cudaStream_t r = open(kGateHeavyEval, 2);
+        if (e != cudaSuccess) return e;
         k_h_eval<<<g2, kBlock, js1, r>>>(a);
         k_h_decide<<<jg, 256, 0, r>>>(a);
+        e = cudaGetLastError();
         close();
         if (e != cudaSuccess) return e;
     }

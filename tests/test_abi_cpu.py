@@ -53,7 +53,7 @@ def test_default_options(native):
     o = native.cc_default_options()
     assert o.max_sweeps == 20 and o.debug_checks == 0 and o.table_log2 == 0 and o.table_start_log2 == 0
     assert o.sweep_mode == 0 and o.lanes == 0 and o.active_set == 0 and o.no_regions == 0
-    assert o.empty_moves == 0 and o.colour_batched == 0 and o.autotune == 0
+    assert o.empty_moves == 0 and o.colour_batched == 0 and o.autotune == 0 and o.tight_rebuild == 0
 
 
 def _create_status(native, n, nnz, row_off, col, k, labels, opt=None):
@@ -86,6 +86,9 @@ def test_host_validation(native):
     assert _create_status(native, 5, 0, ok, None, 1, ok, ctypes.byref(opt))[0] == 1
     opt = native.cc_default_options()
     opt.autotune = 3
+    assert _create_status(native, 5, 0, ok, None, 1, ok, ctypes.byref(opt))[0] == 1
+    opt = native.cc_default_options()
+    opt.tight_rebuild = 3
     assert _create_status(native, 5, 0, ok, None, 1, ok, ctypes.byref(opt))[0] == 1
     opt = native.cc_default_options()
     opt.colour_batched = 2

@@ -94,6 +94,18 @@ def test_batch_mixed_jobs(cc, mode):
         _check_batch(b, jobs, refs)
 
 
+@pytest.mark.parametrize("mode", [0, 2])
+def test_batch_tight_attempt_dropped(cc, mode):
+    """tight_rebuild = 2: every heavy rebuild's tight attempt is dropped and
+    built again at the safe capacity (the second attempt, with the build's
+    part of F' cleared); the jobs still match the oracle."""
+    jobs = _special_jobs() + _mixed_jobs(24, 101)
+    refs = [oracle.sync_run(ro, col, lab, 20) for ro, col, lab in jobs]
+    with cc.ConsensusBatch(jobs, options(cc, sweep_mode=mode, tight_rebuild=2)) as b:
+        assert b.run_until_converged(20) == max(r.sweeps for r in refs)
+        _check_batch(b, jobs, refs)
+
+
 def test_batch_many_small_jobs(cc):
     """Hundreds of jobs of a few hundred vertices: many jobs share each warp."""
     jobs = _mixed_jobs(300, 202, nmax=400)

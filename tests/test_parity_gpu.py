@@ -299,14 +299,17 @@ def test_run_timing_and_launch_count(cc):
         assert len(sweep_ms) == len(prop_ms) == done
         assert np.all(sweep_ms > 0) and np.all(prop_ms > 0) and np.all(prop_ms <= sweep_ms)
         bodies = ((done + 3) // 4) * 4  # graphs of 4 unrolled sweep bodies
-        outside = 15  # per body: begin, own, edges, collect, route, 4 gates, bid, match keys, commit,
+        outside = 17  # per body: begin, own, edges, collect, route, 6 gates, bid, match keys, commit,
         #               match reset, end jobs, end
-        regions = 12 + 9 + 3 + 8  # heavy path, rollback, light path, end-of-sweep rebuild
+        rebuild = 9  # clear, 3 scan kernels, scatter, build, build check, summaries, done
+        # heavy path, its second rebuild attempt, heavy evaluation, rollback,
+        # light path, end-of-sweep rebuild
+        regions = (2 + rebuild) + rebuild + 2 + (1 + rebuild) + 3 + rebuild
         delta = job.launch_count() - base
         assert 1 + bodies * outside < delta < 1 + bodies * (outside + regions)
         # a sweep runs the heavy or the light path, never both, and the
         # skipped bodies after the run stopped enter no region
-        assert delta <= 1 + bodies * outside + done * (12 + 9 + 8)
+        assert delta <= 1 + bodies * outside + done * (regions - 3)
         job.sweep()
         assert len(job.last_run_timing()[0]) == 1
 
@@ -483,10 +486,33 @@ def test_active_set_table_retry(cc):
         assert job.table_stats()["retries"] >= 1
 
 
+@pytest.mark.parametrize("tight", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 2])
+def test_tight_rebuild_same_results(cc, tight, mode):
+    """The heavy sweep's rebuild first tries a tight capacity and builds again
+    at the safe one when the keys do not fit (tight_rebuild = 2 drops every
+    tight attempt, so the second attempt runs); every setting gives the
+    oracle's run, and the tight attempt leaves a smaller table."""
+    c = make_config("lfr", n=20000, k=8, cmin=20, cmax=1000, max_deg=1000, seed=11)
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    ref = oracle.sync_run(ro, col, lab, 20)
+    assert_same(gpu_run(cc, ro, col, lab, 20, sweep_mode=mode, tight_rebuild=tight), ref)
+    caps = []
+    for t in (tight, 1):
+        with cc.Consensus(ro, col, lab, options(cc, sweep_mode=mode, tight_rebuild=t)) as job:
+            job.sweep()  # the singleton start: always the safe capacity
+            assert job.sweep() == ref.stats[1]
+            caps.append(job.table_stats()["capacity"])
+    if tight == 0:
+        assert caps[0] < caps[1]  # the second sweep is heavy and its tight attempt fits
+    else:
+        assert caps[0] == caps[1]
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_no_regions_same_results(cc, mode):
     """Sweep graphs without conditional regions (every kernel a plain node,
-    for profilers) give the same runs; their launch count is 43 kernels per
+    for profilers) give the same runs; their launch count is 55 kernels per
     sweep body."""
     c = make_config("lfr", n=20000, k=8, cmin=20, cmax=1000, max_deg=1000, seed=11)
     ro, col, lab = c["row_off"], c["col"], c["labels"]
@@ -495,7 +521,7 @@ def test_no_regions_same_results(cc, mode):
     with cc.Consensus(ro, col, lab, options(cc, no_regions=1, sweep_mode=mode)) as job:
         base = job.launch_count()
         done = job.run_until_converged(20)
-        assert job.launch_count() - base == 1 + ((done + 3) // 4) * 4 * 43
+        assert job.launch_count() - base == 1 + ((done + 3) // 4) * 4 * 55
 
 
 # --------------------------------------------- move-to-empty variant (option)
