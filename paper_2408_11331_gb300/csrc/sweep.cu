@@ -340,9 +340,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_own(SweepArgs a)
 // chunks of 32 entries are gathered before scoring, so that the scoring
 // rounds (32 / gs candidates each) run nearly full.
 constexpr int kChunks = 4;
+constexpr int kBoundSlots = 64;  // vertices of a window with a per-vertex bound (ids vbase .. vbase + 63)
 struct EdgeScratch {
     int v[32 * kChunks], u[32 * kChunks], x[32 * kChunks], sx[32 * kChunks], sa[32 * kChunks], Aa[32 * kChunks],
         j[32 * kChunks];
+    unsigned long long ubest[kBoundSlots];
+    unsigned char open[32 * kChunks];
 };
 
 // CSR entries 32 at a time per warp: each lane reads one entry (v, u) and
@@ -353,11 +356,12 @@ struct EdgeScratch {
 // singleton {u} is scored from the two label rows; another cluster from its
 // summary rows, then from probes of the open partitions, unless the lower
 // bound on dD from the summary already rules the move out: a bound >= 0 (the
-// move is never proposed), or a packed (bound, C[u]) not below v's least bid
-// so far (bids only decrease, so the move cannot be v's least).  A move with
-// dD < 0 bids its packed (dD, C[u]) at best[v] with an atomic minimum (a
-// candidate kept in two chunks bids the same key twice).  The bids, and so
-// the proposals, do not depend on which candidates the bound skipped.  All group reductions are outside the branches, so every
+// move is never proposed), or a packed (bound, C[u]) not below an upper
+// bound on v's final bid (v's least bid so far, or the summary's upper bound
+// on another of v's candidates).  A move with dD < 0 bids its packed
+// (dD, C[u]) at best[v] with an atomic minimum (a candidate kept in two
+// chunks bids the same key twice).  The bids, and so the proposals, do not
+// depend on which candidates the bounds skipped.  All group reductions are outside the branches, so every
 // lane of the warp takes part in every shuffle.
 template <bool kSingle>
 __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
@@ -475,8 +479,18 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
                 }
             }
         }
-        // other clusters: summary rows, then probes where the bound leaves
-        // the move open
+        // other clusters, in two passes.  Pass 1: the summary rows give each
+        // candidate an exact part and an upper bound ub on A_x, so a least
+        // dD (lo, with A = ub) and a largest one (hi, with A = part); one
+        // that the summary settles (ub == part) bids at once.  The least
+        // packed (hi, x) with hi < 0 over a vertex's candidates of the window
+        // bounds that vertex's final bid from above.  Pass 2: the candidates
+        // whose packed (lo, x) lies below that bound and below the vertex's
+        // least bid so far are listed, and probed in full rounds of gs lanes
+        // each; the others cannot be the vertex's least bid.
+        for (int t = lane; t < kBoundSlots; t += 32) es.ubest[t] = kEmpty;
+        const int vbase = nt > 0 ? es.v[span - 1] : 0;
+        __syncwarp();
         for (int r0 = 0; r0 < nt; r0 += per) {
             const int qq = r0 + lane / gs;
             const bool valid = qq < nt;
@@ -486,24 +500,58 @@ __global__ void __launch_bounds__(kBlock, 4) k_edges(SweepArgs a)
             const JobInfo J = kSingle ? J0 : a.job[valid ? es.j[q] : 0];
             const int k = J.k;
             const int* gv = a.G + row_of(J, valid ? ev : J.vo);
-            // v's least bid so far (read from L2, where the bids land); it
-            // only decreases, so an early read is a valid threshold
-            const unsigned long long cur = valid ? __ldcg(a.best + ev) : 0ull;
-            // part = the exact summary part, ub its upper bound
             int part = 0, ub = 0;
             if (valid) summary_part(a, J, gv, ex_, sx, l, gs, part, ub);
             part = group_sum(part, gs);
             ub = group_sum(ub, gs);
-            // the least dD the probes can give; open only if that could
-            // still be v's least bid
-            const int lb = 2 * (Aa - k - ub) - k * (sa - 1 - sx);
-            const bool open = valid && lb < 0 && pack_key(lb, ex_) < cur;
+            if (valid && l == 0) {
+                const int base = 2 * (Aa - k) - k * (sa - 1 - sx);  // dD = base - 2 A
+                const int lo = base - 2 * ub, hi = base - 2 * part;
+                const unsigned d = (unsigned)(ev - vbase);
+                if (hi < 0 && d < (unsigned)kBoundSlots) atomicMin(&es.ubest[d], pack_key(hi, ex_));
+                if (ub == part) {
+                    if (lo < 0) atomicMin(&a.best[ev], pack_key(lo, ex_));
+                    es.u[q] = 0;  // settled
+                } else {
+                    es.u[q] = lo;
+                    es.sa[q] = base;
+                    es.Aa[q] = part;
+                }
+            }
+        }
+        __syncwarp();
+        int no = 0;
+        for (int c0 = 0; c0 < nt; c0 += 32) {
+            const int qq = c0 + lane;
+            const int q = (int)span - 1 - qq;
+            bool open = false;
+            if (qq < nt) {
+                const int lo = es.u[q];
+                if (lo < 0) {
+                    const int ev = es.v[q];
+                    const unsigned d = (unsigned)(ev - vbase);
+                    unsigned long long thr = __ldcg(a.best + ev);
+                    if (d < (unsigned)kBoundSlots && es.ubest[d] < thr) thr = es.ubest[d];
+                    open = pack_key(lo, es.x[q]) < thr;
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, open);
+            if (open) es.open[no + __popc(bal & lt)] = (unsigned char)q;
+            no += __popc(bal);
+        }
+        __syncwarp();
+        for (int r0 = 0; r0 < no; r0 += per) {
+            const int qi = r0 + lane / gs;
+            const bool valid = qi < no;
+            const int q = valid ? (int)es.open[qi] : 0;
+            const int ev = valid ? es.v[q] : 0, ex_ = valid ? es.x[q] : 0, sx = valid ? es.sx[q] : 0;
+            const JobInfo J = kSingle ? J0 : a.job[valid ? es.j[q] : 0];
+            const int* gv = a.G + row_of(J, valid ? ev : J.vo);
             int pb = 0;
-            if (open) pb = probe_part(a, J, a.table, mask, gv, ex_, sx, l, gs);
+            if (valid) pb = probe_part(a, J, a.table, mask, gv, ex_, sx, l, gs);
             pb = group_sum(pb, gs);
-            if (open && l == 0) {
-                const int A = part + pb;
-                const int dD = 2 * (Aa - k - A) - k * (sa - 1 - sx);
+            if (valid && l == 0) {
+                const int dD = es.sa[q] - 2 * (es.Aa[q] + pb);
                 if (dD < 0) atomicMin(&a.best[ev], pack_key(dD, ex_));
             }
         }
