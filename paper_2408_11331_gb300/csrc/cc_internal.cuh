@@ -396,6 +396,31 @@ __device__ __forceinline__ ulonglong2 entry_cas(int4* p, ulonglong2 cmp, ulonglo
 // mark (0 or 1) goes into the new slot's staged-delta field: the rebuild
 // marks the keys whose summary entry is already final (see setup.cu) and
 // clears the mark again before any sweep stages deltas.
+// The rest of an insert whose first CAS, at key's home slot h, returned old
+// (so that a warp can have the first CASes of several keys in flight).
+__device__ __forceinline__ long long table_build_finish(Slot* t, unsigned long long mask, unsigned long long key,
+                                                        int cnt, bool* inserted, int mark, unsigned long long limit,
+                                                        unsigned long long h, ulonglong2 old)
+{
+    *inserted = false;
+    const ulonglong2 empty = make_ulonglong2(kEmpty, 0ull);
+    const ulonglong2 mine =
+        make_ulonglong2(key, ((unsigned long long)(unsigned)mark << 32) | (unsigned long long)(unsigned)cnt);
+    for (unsigned long long p = 0;;) {
+        if (old.x == kEmpty && old.y == 0ull) {
+            *inserted = true;
+            return (long long)h;
+        }
+        if (old.x == key) {
+            atomicAdd(&t[h].cnt, cnt);
+            return (long long)h;
+        }
+        if (++p > mask || p >= limit) return -1;
+        h = (h + 1) & mask;
+        old = slot_cas(t + h, empty, mine);
+    }
+}
+
 __device__ __forceinline__ long long table_build_add(Slot* t, unsigned long long mask, unsigned long long key, int cnt,
                                                      bool* inserted, int mark = 0, unsigned long long limit = ~0ull)
 {

@@ -422,7 +422,7 @@ __device__ __forceinline__ unsigned long long segment_max(unsigned long long x, 
 // the warps stop inserting.
 constexpr unsigned long long kTightProbes = 256;
 
-__global__ void k_table_build(SweepArgs a, int conditional, int eval)
+__global__ void __launch_bounds__(kSetupBlock, 4) k_table_build(SweepArgs a, int conditional, int eval)
 {
     extern __shared__ long long dyn_jobs[];
     DevState* st = a.st;
@@ -460,34 +460,64 @@ __global__ void k_table_build(SweepArgs a, int conditional, int eval)
             if (whole) seg_end = (int)(end - wb);
             S = a.summ + row_of(J, c);
         }
-        const bool head = whole && (m == (long long)a.cursor[c] - a.size[c]);
-        for (int i = 0; i < a.kmax; ++i) {
-            const bool on = valid && i < k;
-            const int g = on ? row[i] : 0;
-            const unsigned long long key = on ? ckey(c, g) : kEmpty;
-            const unsigned same = __match_any_sync(0xffffffffu, key);
-            const int cnt = __popc(same);
-            const bool leader = on && (__ffs(same) - 1) == lane;
-            bool ins = false;
-            if (leader) {
-                if (table_build_add(a.table, mask, key, cnt, &ins, whole ? 1 : 0, limit) < 0) {
-                    if (tight) st->build_fail = 1;
-                    else set_err(st, CC_ERR_TABLE_FULL);
-                }
-                if (ev && whole) acc.add(job, -2LL * cnt * cnt);
+        const int hl = whole ? (int)((long long)a.cursor[c] - a.size[c] - wb) : lane;  // the cluster's first lane
+        const bool head = whole && hl == lane;
+        // the warp's whole clusters need the summary maxima; a warp without
+        // any skips them
+        const bool any_whole = __any_sync(0xffffffffu, whole);
+        const int4* G4 = reinterpret_cast<const int4*>(row);
+        const ulonglong2 empty = make_ulonglong2(kEmpty, 0ull);
+        const unsigned long long mark = whole ? (1ull << 32) : 0ull;
+        // four partitions at a time: one quad of the label row, and the four
+        // keys' first CASes issued before any result is used
+        for (int i0 = 0; i0 < a.kmax; i0 += 4) {
+            int4 g4 = make_int4(0, 0, 0, 0);
+            if (valid && i0 < k) g4 = __ldg(G4 + (i0 >> 2));
+            const int gq[4] = {g4.x, g4.y, g4.z, g4.w};
+            unsigned long long key[4], h[4];
+            int cnt[4];
+            bool lead[4];
+            ulonglong2 old[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const bool on = valid && i0 + b < k;
+                key[b] = on ? ckey(c, gq[b]) : kEmpty;
+                const unsigned same = __match_any_sync(0xffffffffu, key[b]);
+                cnt[b] = __popc(same);
+                lead[b] = on && (__ffs(same) - 1) == lane;
+                h[b] = hash_key(key[b]) & mask;
             }
-            used += __popc(__ballot_sync(0xffffffffu, ins));
-            // summary entry of a whole cluster: the two largest (count, label)
-            const unsigned long long mine =
-                (whole && on) ? ((unsigned long long)(unsigned)cnt << 32) | (unsigned)g : 0ull;
-            const unsigned long long top1 = segment_max(mine, lane, seg_end);
-            const int hl = whole ? (int)((long long)a.cursor[c] - a.size[c] - wb) : lane;
-            const unsigned long long t1 = __shfl_sync(0xffffffffu, top1, hl);
-            const unsigned long long other = (mine != 0 && (unsigned)mine != (unsigned)t1) ? mine : 0ull;
-            const unsigned long long top2 = segment_max(other, lane, seg_end);
-            if (head && on) {
-                const int d2 = top2 ? (int)(unsigned)top2 : -1, m2 = (int)(top2 >> 32);
-                S[i] = make_int4((int)(unsigned)top1, (int)(top1 >> 32), d2, m2);
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (lead[b]) old[b] = slot_cas(a.table + h[b], empty, make_ulonglong2(key[b], mark | (unsigned)cnt[b]));
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                bool ins = false;
+                if (lead[b]) {
+                    if (table_build_finish(a.table, mask, key[b], cnt[b], &ins, whole ? 1 : 0, limit, h[b], old[b]) <
+                        0) {
+                        if (tight) st->build_fail = 1;
+                        else set_err(st, CC_ERR_TABLE_FULL);
+                    }
+                    if (ev && whole) acc.add(job, -2LL * cnt[b] * cnt[b]);
+                }
+                used += __popc(__ballot_sync(0xffffffffu, ins));
+            }
+            if (!any_whole) continue;
+            // summary entries of the whole clusters: the two largest (count, label)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const bool on = valid && i0 + b < k;
+                const unsigned long long mine =
+                    (whole && on) ? ((unsigned long long)(unsigned)cnt[b] << 32) | (unsigned)gq[b] : 0ull;
+                const unsigned long long top1 = segment_max(mine, lane, seg_end);
+                const unsigned long long t1 = __shfl_sync(0xffffffffu, top1, hl);
+                const unsigned long long other = (mine != 0 && (unsigned)mine != (unsigned)t1) ? mine : 0ull;
+                const unsigned long long top2 = segment_max(other, lane, seg_end);
+                if (head && on) {
+                    const int d2 = top2 ? (int)(unsigned)top2 : -1, m2 = (int)(top2 >> 32);
+                    S[i0 + b] = make_int4((int)(unsigned)top1, (int)(top1 >> 32), d2, m2);
+                }
             }
         }
     }
