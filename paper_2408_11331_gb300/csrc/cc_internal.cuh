@@ -391,13 +391,13 @@ __device__ __forceinline__ ulonglong2 entry_cas(int4* p, ulonglong2 cmp, ulonglo
 // Adds cnt to key's count in a table being built from a cleared state (every
 // slot either empty with count 0, or holding a key): a new key is written
 // together with its count by one 16-byte CAS; an existing key gets an atomic
-// add.  *inserted is set when this call created the slot.  Returns -1 if the
-// key found no slot within `limit` probes (the whole table by default).
+// add.  The caller issues the first CAS, at key's home slot h (so that a warp
+// can have the first CASes of several keys in flight), and passes its result
+// as old; this finishes the insert.  *inserted is set when the insert created
+// the slot.  Returns -1 if the key found no slot within `limit` probes.
 // mark (0 or 1) goes into the new slot's staged-delta field: the rebuild
 // marks the keys whose summary entry is already final (see setup.cu) and
 // clears the mark again before any sweep stages deltas.
-// The rest of an insert whose first CAS, at key's home slot h, returned old
-// (so that a warp can have the first CASes of several keys in flight).
 __device__ __forceinline__ long long table_build_finish(Slot* t, unsigned long long mask, unsigned long long key,
                                                         int cnt, bool* inserted, int mark, unsigned long long limit,
                                                         unsigned long long h, ulonglong2 old)
@@ -419,29 +419,6 @@ __device__ __forceinline__ long long table_build_finish(Slot* t, unsigned long l
         h = (h + 1) & mask;
         old = slot_cas(t + h, empty, mine);
     }
-}
-
-__device__ __forceinline__ long long table_build_add(Slot* t, unsigned long long mask, unsigned long long key, int cnt,
-                                                     bool* inserted, int mark = 0, unsigned long long limit = ~0ull)
-{
-    *inserted = false;
-    const ulonglong2 empty = make_ulonglong2(kEmpty, 0ull);
-    const ulonglong2 mine =
-        make_ulonglong2(key, ((unsigned long long)(unsigned)mark << 32) | (unsigned long long)(unsigned)cnt);
-    unsigned long long h = hash_key(key) & mask;
-    for (unsigned long long p = 0; p <= mask && p < limit; ++p) {
-        const ulonglong2 old = slot_cas(t + h, empty, mine);
-        if (old.x == kEmpty && old.y == 0ull) {
-            *inserted = true;
-            return (long long)h;
-        }
-        if (old.x == key) {
-            atomicAdd(&t[h].cnt, cnt);
-            return (long long)h;
-        }
-        h = (h + 1) & mask;
-    }
-    return -1;
 }
 
 // ---- setup.cu ----
