@@ -62,8 +62,12 @@ UNIT = "edge-partitions/s"
 # case of the same workload, scaled by nnz to the full size; reported as
 # roofline.traffic while the kernels are the ones captured (empty when they
 # changed since).
-PROPOSAL_TRAFFIC = {}
-PROPOSAL_TRAFFIC_SOURCE = {}
+PROPOSAL_TRAFFIC = {"knn_n2000000_k50": 47.90e9, "lfr_n1000000_k20": 3.648e9}
+PROPOSAL_TRAFFIC_SOURCE = {
+    "knn_n2000000_k50": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_own, k_edges, k_collect over one "
+                        "run at n=500000 (11.706 GB), scaled by nnz (x4.0921)",
+    "lfr_n1000000_k20": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_own, k_edges, k_collect over one "
+                        "run at n=500000 (1.824 GB), scaled by nnz (x2.0002)"}
 
 
 def parse():
@@ -480,6 +484,34 @@ def single_job(args, c, local, dist, rank, world, extras=True):
                          "note": "cc_options.active_set = 1: after a run's first sweep, a vertex whose cluster and "
                                  "previous target did not change scores only its candidates whose cluster changed; "
                                  "fewer edges evaluated, identical results"}
+
+    # the two variants of the method (options that change the results; their
+    # parity with the oracle is tested at smaller sizes), one timed run each
+    # beside the synchronous run's F and sweeps
+    F_sync = int(job.objective())
+    variants = {"synchronous": {"F": F_sync, "sweeps": len(job.history()), "ms_per_run": ms / steps}}
+    for name in ("colour_batched", "empty_moves"):
+        ov = ccg.cc_default_options()
+        setattr(ov, name, 1)
+        ov.no_regions = opts.no_regions
+        with ccg.Consensus(ro, col, lab, ov) as jv:
+            jv.set_stream(stream.cuda_stream)
+            jv.run_until_converged(args.max_sweeps)
+            jv.reset()
+            torch.cuda.synchronize()
+            ev4 = torch.cuda.Event(enable_timing=True)
+            ev5 = torch.cuda.Event(enable_timing=True)
+            ev4.record(stream)
+            jv.run_until_converged(args.max_sweeps)
+            ev5.record(stream)
+            torch.cuda.synchronize()
+            Fv = int(jv.objective())
+            variants[name] = {"F": Fv, "sweeps": len(jv.history()), "ms_per_run": ev4.elapsed_time(ev5),
+                              "F_over_synchronous": Fv / F_sync if F_sync else None}
+    variants["note"] = ("colour_batched: colour classes of a greedy colouring run in turn, each class's moves "
+                        "applied before the next proposes; empty_moves: a vertex may also move into a new "
+                        "cluster of its own")
+    out["variants"] = variants
 
     # partition distances of the consensus to each input partition (Methods,
     # Evaluation metrics), timed on the host around a synchronous call
