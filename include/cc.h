@@ -327,9 +327,10 @@ cc_status cc_table_stats(cc_ctx* ctx, cc_table_info* out);
  * launched directly, every kernel node of its sweep graphs that sits outside
  * a conditional region (whether or not a stopped sweep returned from it at
  * once), and the kernels of the conditional regions that ran (the heavy
- * path, its rollback, the light path and the end-of-sweep rebuild of a sweep
- * are IF nodes, entered only when needed; their gates count them on the
- * device).  Synchronises the context's stream. */
+ * path, the second attempt of its rebuild, its evaluation, its rollback, the
+ * light path and the end-of-sweep rebuild of a sweep are IF nodes, entered
+ * only when needed; their gates count them on the device).  Synchronises the
+ * context's stream. */
 cc_status cc_launch_count(const cc_ctx* ctx, int64_t* out);
 
 /* Copies the records of the sweeps run since creation or the last reset,
