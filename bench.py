@@ -836,8 +836,8 @@ def run_mix_reference(args, rank, kind, specs, member, pool, gen_s):
 
 def compact(part):
     """The summary of an extra single-job workload kept in the headline line."""
-    keep = ("value", "unit", "ms_per_step", "steps", "roofline", "e2e", "cpu_baseline", "active_set", "clocks",
-            "gpu_launches")
+    keep = ("value", "unit", "ms_per_step", "steps", "roofline", "e2e", "cpu_baseline", "active_set", "variants",
+            "clocks", "gpu_launches")
     d = {key: part.get(key) for key in keep}
     d["workload"] = part["config"]["workload"]
     d["description"] = part["config"]["description"]
