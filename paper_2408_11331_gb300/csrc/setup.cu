@@ -429,7 +429,9 @@ __global__ void __launch_bounds__(kSetupBlock, 4) k_table_build(SweepArgs a, int
     if (rebuild_off(st, conditional)) return;
     __shared__ unsigned long long s_used;
     if (threadIdx.x == 0) s_used = 0;
-    const bool tight = st->tight != 0;
+    // tight attempts are made only by the heavy sweep's rebuild inside a
+    // sweep graph; a rebuild the host asks for is never one
+    const bool tight = conditional && st->tight != 0;
     const unsigned long long limit = tight ? kTightProbes : ~0ull;
     const bool ev = eval && st->heavy;
     JobAcc acc(ev ? job_smem_init(a.jobs, dyn_jobs) : nullptr, &a.js[0].recompute, kJobStride);
@@ -592,7 +594,7 @@ __global__ void k_build_check(SweepArgs a, int conditional)
     __shared__ int fail;
     if (threadIdx.x == 0) {
         fail = 0;
-        if (st->tight) {
+        if (conditional && st->tight) {
             const unsigned long long cap = st->new_mask + 1, fill = cap - (cap >> 3);
             const unsigned long long room = 2 * ((a.keys + 7) / 8);
             fail = st->build_fail || st->used > cap / 2 || st->used + room > fill || a.tight_mode == 2;
