@@ -275,6 +275,16 @@ cc_status cc_job_history(cc_ctx* ctx, int32_t job, int32_t max, cc_sweep_info* o
  * cc_consensus_labels of that job alone. */
 cc_status cc_job_labels(cc_ctx* ctx, int32_t job, int32_t* out);
 
+/* The batch calls under the names of the interface's first description
+ * (a batch context is a cc_ctx from cc_batch_create):
+ * cc_batch_run  = cc_run_until_converged without the sweep count: the whole
+ *                 run of every job (one graph launch for a batch context).
+ * cc_batch_result = job `job`'s consensus labels (int32[n_j] host, as
+ *                 cc_job_labels) and objective (as cc_job_objective); either
+ *                 output may be NULL, not both.  Errors as those calls. */
+cc_status cc_batch_run(cc_ctx* ctx, int32_t max_sweeps);
+cc_status cc_batch_result(cc_ctx* ctx, int32_t job, int32_t* labels_out, int64_t* objective_out);
+
 /* Uses the given cudaStream_t (NULL: the context's own) for later calls. */
 cc_status cc_set_stream(cc_ctx* ctx, void* stream);
 

@@ -24,6 +24,7 @@ EXPORTS = ("cc_default_options", "cc_create", "cc_create_dev", "cc_set_stream", 
            "cc_run_until_converged", "cc_last_run_timing", "cc_table_stats", "cc_launch_count", "cc_history", "cc_objective", "cc_objective_recompute",
            "cc_consensus_labels", "cc_cluster_ids", "cc_cluster_ids_dev", "cc_last_error", "cc_destroy",
            "cc_batch_create", "cc_job_count", "cc_job_objective", "cc_job_history", "cc_job_labels",
+           "cc_batch_run", "cc_batch_result",
            "cc_metrics", "cc_partition_distances", "cc_group_partitions", "cc_estimate_bytes", "cc_plan_batches", "cc_server_default_options", "cc_server_create", "cc_server_submit",
            "cc_server_progress", "cc_server_job", "cc_server_stats", "cc_server_last_error", "cc_server_destroy",
            "cc_renumber_noalloc", "cc_noalloc_max_n", "cc_autotune_record")
@@ -140,6 +141,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.cc_job_history.argtypes = [P, c.c_int32, c.c_int32, c.POINTER(cc_sweep_info), c.POINTER(c.c_int32)]
     lib.cc_job_labels.restype = c.c_int
     lib.cc_job_labels.argtypes = [P, c.c_int32, P]
+    lib.cc_batch_run.restype = c.c_int
+    lib.cc_batch_run.argtypes = [P, c.c_int32]
+    lib.cc_batch_result.restype = c.c_int
+    lib.cc_batch_result.argtypes = [P, c.c_int32, P, c.POINTER(c.c_int64)]
     lib.cc_metrics.restype = c.c_int
     lib.cc_metrics.argtypes = [P, c.POINTER(cc_partition_metrics)]
     lib.cc_partition_distances.restype = c.c_int
@@ -277,6 +282,18 @@ def cc_job_labels(ctx, job: int, n: int, out: np.ndarray | None = None) -> np.nd
     out = np.empty(n, np.int32) if out is None else out
     _check(lib.cc_job_labels(ctx, job, _ptr(out)), ctx)
     return out
+
+
+def cc_batch_run(ctx, max_sweeps: int = 0):
+    _check(lib.cc_batch_run(ctx, max_sweeps), ctx)
+
+
+def cc_batch_result(ctx, job: int, n: int) -> tuple[np.ndarray, int]:
+    """(labels int32[n], objective) of job `job`."""
+    out = np.empty(n, np.int32)
+    obj = ctypes.c_int64(0)
+    _check(lib.cc_batch_result(ctx, job, _ptr(out), ctypes.byref(obj)), ctx)
+    return out, int(obj.value)
 
 
 def cc_set_stream(ctx, stream: int = 0):

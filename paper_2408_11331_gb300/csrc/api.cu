@@ -1798,6 +1798,21 @@ cc_status cc_job_labels(cc_ctx* c, int32_t job, int32_t* out)
     return CC_OK;
 }
 
+cc_status cc_batch_run(cc_ctx* c, int32_t max_sweeps)
+{
+    return cc_run_until_converged(c, max_sweeps, nullptr);
+}
+
+cc_status cc_batch_result(cc_ctx* c, int32_t job, int32_t* labels_out, int64_t* objective_out)
+{
+    if (!c) return fail(nullptr, CC_ERR_INVALID, "ctx is NULL");
+    if (!labels_out && !objective_out) return fail(c, CC_ERR_INVALID, "both outputs are NULL");
+    cc_status r = CC_OK;
+    if (labels_out) r = cc_job_labels(c, job, labels_out);
+    if (r == CC_OK && objective_out) r = cc_job_objective(c, job, objective_out, nullptr);
+    return r;
+}
+
 cc_status cc_metrics(cc_ctx* c, cc_partition_metrics* out)
 {
     if (!c || !out) return fail(c, CC_ERR_INVALID, "null argument");

@@ -161,6 +161,8 @@ def test_batch_null_context_calls(native):
     assert lib.cc_job_objective(None, 0, ctypes.byref(out), None) == 1
     assert lib.cc_job_history(None, 0, 0, None, ctypes.byref(n)) == 1
     assert lib.cc_job_labels(None, 0, None) == 1
+    assert lib.cc_batch_run(None, 0) == 1
+    assert lib.cc_batch_result(None, 0, None, ctypes.byref(out)) == 1
 
 
 def test_python_batch_binding_checks_shapes(native):

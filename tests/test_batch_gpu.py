@@ -106,6 +106,23 @@ def test_batch_tight_attempt_dropped(cc, mode):
         _check_batch(b, jobs, refs)
 
 
+def test_batch_run_and_result_names(cc):
+    """cc_batch_run and cc_batch_result (the batch interface under its first
+    names) give the oracle's run, as cc_run_until_converged, cc_job_labels and
+    cc_job_objective do."""
+    from paper_2408_11331_gb300 import _native
+
+    jobs = _mixed_jobs(6, 303)
+    refs = [oracle.sync_run(ro, col, lab, 20) for ro, col, lab in jobs]
+    with cc.ConsensusBatch(jobs) as b:
+        _native.cc_batch_run(b._ctx, 20)
+        for j, ref in enumerate(refs):
+            lab, F = _native.cc_batch_result(b._ctx, j, b.sizes[j])
+            np.testing.assert_array_equal(lab, oracle.renumber(ref.C), err_msg=f"job {j}")
+            assert F == ref.F, f"job {j}"
+            assert b.sweeps(j) == ref.sweeps, f"job {j}"
+
+
 def test_batch_many_small_jobs(cc):
     """Hundreds of jobs of a few hundred vertices: many jobs share each warp."""
     jobs = _mixed_jobs(300, 202, nmax=400)
