@@ -62,6 +62,8 @@ UNIT = "edge-partitions/s"
 # case of the same workload, scaled by nnz to the full size; reported as
 # roofline.traffic while the kernels are the ones captured (empty when they
 # changed since).
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the roofline's peak is the measured copy rate)
+
 PROPOSAL_TRAFFIC = {"knn_n2000000_k50": 47.90e9, "lfr_n1000000_k20": 3.648e9}
 PROPOSAL_TRAFFIC_SOURCE = {
     "knn_n2000000_k50": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_own, k_edges, k_collect over one "
@@ -426,6 +428,7 @@ def single_job(args, c, local, dist, rank, world, extras=True):
         "dram_frac": (traffic / (prop_total_ms / 1e3) / 1e9 / peak) if traffic else None,
         "traffic_source": PROPOSAL_TRAFFIC_SOURCE.get(c["name"]),
         "peak_source": peak_src,
+        "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
         "algorithmic_bytes_per_step": int(np.sum(balg[:n_sw])),
         "propose_ms_per_step": prop_total_ms}
 
