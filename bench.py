@@ -307,6 +307,29 @@ def cpu_baseline(c, job, budget_s):
             "parity": (f"bit-exact ({what}: every sweep record and the raw cluster ids)" if same else "MISMATCH")}, C
 
 
+def single_thread_sample(c, target_s=1.0):
+    """The oracle's proposal pass (every vertex's best move against the
+    singleton start) on one host thread, over the first vertices of the job:
+    the block doubles from n/256 until it takes target_s or covers n/8."""
+    import oracle
+
+    ro, col, lab = c["row_off"], c["col"], c["labels"]
+    k, n = lab.shape
+    C0 = oracle.singletons(n)
+    nb = max(1, n // 256)
+    while True:
+        t0 = time.perf_counter()
+        oracle.sync_propose_range(ro, col, lab, C0, 0, nb, threads=1)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or nb >= max(1, n // 8):
+            break
+        nb = min(2 * nb, max(1, n // 8))
+    units = float(ro[nb] - ro[0]) * k
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "seconds": round(dt, 3),
+            "sample": f"proposal pass of vertices [0, {nb}) against the singleton start on one thread; "
+                      f"units = their CSR entries x k"}
+
+
 def over_ranks(dist, seconds, units, device):
     """Whole-job figures of N replicas: the slowest rank's time and the units
     of all ranks (each rank runs its own copy of the job; nothing else is
@@ -541,6 +564,7 @@ def single_job(args, c, local, dist, rank, world, extras=True):
         import oracle
 
         cpu, _ = cpu_baseline(c, job, args.cpu_seconds)
+        cpu["single_thread"] = single_thread_sample(c)
         job.reset()
         job.run_until_converged(args.max_sweeps)
         C_gpu = job.cluster_ids()

@@ -54,6 +54,18 @@ def _bench_module():
     return bench
 
 
+def test_single_thread_sample():
+    """The single-thread oracle sample beside the all-core baseline."""
+    sys.path.insert(0, ROOT)
+    from workloads import make_config
+
+    bench = _bench_module()
+    c = make_config("sbm")
+    s = bench.single_thread_sample(c, target_s=0.01)
+    assert s["cores"] == 1 and s["value"] > 0 and s["unit"] == bench.UNIT
+    assert "one thread" in s["sample"]
+
+
 def test_byte_model_counts_candidates():
     """The roofline's algorithmic bytes: distinct (vertex, other cluster)
     pairs over the CSR and the per-candidate unit costs, checked against a
